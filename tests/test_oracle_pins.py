@@ -1,0 +1,451 @@
+"""Pins of the FP64 oracle against closed forms, the mathematics and brute force (no GPU).
+
+Each test checks the oracle against something other than itself: the Morse pair potential
+differentiated numerically on a periodic supercell, closed-form frequencies, exact symmetries,
+a brute-force enumeration, band folding, and exact identities of a quadratic form."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import diamond_crystal, morse_ifcs, morse_system, supercell_crystal, MorseParams
+from tests.fd_energy import SupercellEnergy
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+@pytest.fixture(scope="module")
+def sys0():
+    return morse_system(seed=0)
+
+
+@pytest.fixture(scope="module")
+def sys_clean():
+    return morse_system(seed=0, perturb=0.0)
+
+
+@pytest.fixture(scope="module")
+def prob3(sys0):
+    return oracle.Problem(*sys0, (3, 3, 3))
+
+
+# ------------------------------------------------------------------------------ units
+
+def test_unit_constants_two_routes():
+    """Γ prefactors through SI and through amu-Å-ps natural units agree."""
+    a = oracle.unit_constants_si()
+    b = oracle.unit_constants_natural()
+    for x, y in zip(a, b):
+        assert abs(x - y) <= 1e-14 * abs(x)
+    # eigenvalue conversion: 1 eV/(Å² amu) = (e / amu) * 1e-4 (rad/ps)², close to F / 10 C/g
+    assert abs(oracle.EIG_TO_RADPS2 - 9648.5332) < 1e-3
+
+
+# ------------------------------------------------------------------------------ harmonic
+
+@pytest.mark.parametrize("seed,n", [(0, 8), (1, 8), (1, 16)])
+def test_crystal_stable(seed, n):
+    """The Morse diamond crystal (Φ2 from the first shell) has no imaginary mode."""
+    c, p2, p3, p4 = morse_system(seed=seed)
+    m = oracle.harmonic(c, p2, (n, n, n))
+    assert m.eig[1:].min() > 0.0
+    assert np.abs(m.eig[0, :3]).max() < 1e-12        # acoustic sum rule at Γ
+
+
+def test_gamma_optical_closed_form(sys_clean):
+    """Unperturbed first-shell central-force diamond: ω_opt(Γ)² = (2/m)(4/3 k_r + 8/3 k_t),
+    k_r = φ''(r1), k_t = φ'(r1)/r1 (triply degenerate)."""
+    c, p2, _, _ = sys_clean
+    r1 = 5.43 * math.sqrt(3) / 4
+    d1, d2, _, _ = MorseParams().radial_derivatives(r1)
+    w2 = 2.0 / c.masses[0] * (4.0 / 3.0 * d2 + 8.0 / 3.0 * d1 / r1) * oracle.EIG_TO_RADPS2
+    m = oracle.harmonic(c, p2, (1, 1, 1))
+    assert np.allclose(m.omega[3:6] ** 2, w2, rtol=1e-12)
+
+
+def test_group_velocity_finite_difference(sys0):
+    """v = dω/dq (Hellmann-Feynman) vs central differences of ω along each axis (non-degenerate)."""
+    c, p2, _, _ = sys0
+    q0 = np.array([0.13, 0.07, 0.21])
+    h = 1e-6
+    D, dD = oracle.dynamical_matrix(c, p2, q0)
+    lam, v = np.linalg.eigh(D)
+    j = 5
+    w = math.sqrt(lam[j] * oracle.EIG_TO_RADPS2)
+    g = np.array([np.real(np.conj(v[:, j]) @ dD[x] @ v[:, j]) for x in range(3)])
+    vel = g * oracle.EIG_TO_RADPS2 / (2 * w)
+    for x in range(3):
+        dq = np.zeros(3)
+        dq[x] = h
+        lp = np.linalg.eigh(oracle.dynamical_matrix(c, p2, q0 + dq)[0])[0][j]
+        lm = np.linalg.eigh(oracle.dynamical_matrix(c, p2, q0 - dq)[0])[0][j]
+        fd = (math.sqrt(lp * oracle.EIG_TO_RADPS2) - math.sqrt(lm * oracle.EIG_TO_RADPS2)) / (2 * h)
+        assert abs(fd - vel[x]) < 1e-6 * max(1.0, abs(vel[x]))
+
+
+# ------------------------------------------------------------------------------ matrix elements
+
+def _fd_problem():
+    c, p2, p3, p4 = morse_system(seed=0, perturb=0.0)
+    P = oracle.Problem(c, p2, p3, p4, (3, 3, 3))
+    return c, P, SupercellEnergy(c, 3)
+
+
+def test_v3_equals_supercell_third_derivative():
+    """Re and Im of V3+(λ, λ', λ'') at finite q equal (4/N_cells) ∂³E/∂t1∂t2∂t3 of the Morse energy
+    of a 3x3x3 supercell displaced along Re/Im(e/sqrt(m) exp(iq.R)) of the three modes."""
+    c, P, S = _fd_problem()
+    nb, qs = P.nb, oracle.q_cart(c.lattice, P.mesh)
+    q1, q2 = 1, 3                            # (1,0,0)/3 and (0,1,0)/3
+    q3 = 1 + 3 * 1                           # q1 + q2 = (1,1,0)/3
+    for (j1, j2, j3) in [(3, 4, 5), (1, 5, 2), (4, 0, 3)]:
+        m1, m2, m3 = q1 * nb + j1, q2 * nb + j2, q3 * nb + j3
+        V = P.v3(+1, m1, m2, m3)
+        e1, e2, e3 = P.modes.evec[q1][:, j1], P.modes.evec[q2][:, j2], P.modes.evec[q3][:, j3]
+        p1, p2_ = S.pattern(e1, qs[q1]), S.pattern(e2, qs[q2])
+        re = S.mixed_derivative([p1, p2_, S.pattern(e3, qs[q3])], 0.05)
+        im = S.mixed_derivative([p1, p2_, S.pattern(e3, qs[q3], imag=True)], 0.05)
+        scale = S.ncell / 4.0
+        assert abs(re - scale * V.real) < 2e-6 * scale * abs(V)
+        # the Im pattern is Re(-i ũ e^{iqR}); its conjugate leg carries +i, giving -Im V
+        assert abs(im + scale * V.imag) < 2e-6 * scale * abs(V)
+
+
+def test_v4_equals_supercell_fourth_derivative():
+    """Re V4++(λ, λ', λ'', λ''') at finite q equals (8/N_cells) ∂⁴E of the supercell energy."""
+    c, P, S = _fd_problem()
+    nb, qs = P.nb, oracle.q_cart(c.lattice, P.mesh)
+    q1, q2, q3 = 1, 3, 9                     # unit steps along b1, b2, b3 (over 3)
+    q4 = 1 + 3 * (1 + 3 * 1)                 # (1,1,1)/3
+    for (j1, j2, j3, j4) in [(3, 4, 5, 3), (1, 2, 5, 4)]:
+        ms = [q1 * nb + j1, q2 * nb + j2, q3 * nb + j3, q4 * nb + j4]
+        V = P.v4(+1, +1, *ms)
+        pats = [S.pattern(P.modes.evec[q][:, j], qs[q]) for q, j in
+                [(q1, j1), (q2, j2), (q3, j3), (q4, j4)]]
+        re = S.mixed_derivative(pats, 0.06)
+        scale = S.ncell / 8.0
+        assert abs(re - scale * V.real) < 1e-5 * scale * abs(V)
+
+
+def test_v_vanishes_for_acoustic_partner_at_gamma(prob3):
+    """A uniform translation (Γ acoustic partner, e ∝ sqrt(m) u) decouples under the acoustic sum
+    rule: V3 = 0 and V4 = 0 for any other legs."""
+    P = prob3
+    nb = P.nb
+    for jac in range(3):
+        for (m0, m2) in [(1 * nb + 4, 1 * nb + 2), (5 * nb + 3, 5 * nb + 5)]:
+            v = P.v3(+1, m0, jac, m2)
+            ref = abs(P.v3(+1, m0, 4, m2))
+            assert abs(v) < 1e-12 * max(ref, 1.0)
+        v4 = P.v4(+1, -1, 1 * nb + 4, jac, 7 * nb + 2, 1 * nb + 3)
+        assert abs(v4) < 1e-11
+
+
+def test_v_time_reversal(sys0):
+    """With e(-q) = conj(e(q)): V3-(λ, λ', λ'') = V3+(λ, -λ', λ'') and
+    V4^(s1,s2) flips the same way leg by leg."""
+    c, p2, p3, p4 = sys0
+    mesh = (3, 3, 3)
+    base = oracle.harmonic(c, p2, mesh)
+    qc = oracle.q_coords(mesh)
+    minus = [int(((-x) % 3) + 3 * (((-y) % 3) + 3 * ((-z) % 3))) for x, y, z in qc]
+    ev = base.evec.copy()
+    for iq in range(27):
+        if minus[iq] > iq:
+            ev[minus[iq]] = np.conj(ev[iq])
+    modes = oracle.Modes(base.omega, base.vel, ev, base.eig)
+    P = oracle.Problem(c, p2, p3, p4, mesh, modes=modes)
+    nb = P.nb
+    q, q1 = 4, 11
+    q2 = oracle.q_coords(mesh)
+    for (j, j1, j2) in [(3, 4, 5), (2, 1, 0)]:
+        m0 = q * nb + j
+        m1 = q1 * nb + j1
+        m1m = minus[q1] * nb + j1
+        m2 = 13 * nb + j2
+        assert abs(P.v3(-1, m0, m1, m2) - P.v3(+1, m0, m1m, m2)) < 1e-12 * abs(P.v3(-1, m0, m1, m2)) + 1e-14
+        m3 = 20 * nb + 5
+        a = P.v4(-1, -1, m0, m1, 7 * nb + j2, m3)
+        b = P.v4(+1, +1, m0, m1m, minus[7] * nb + j2, m3)
+        assert abs(a - b) < 1e-12 * abs(a) + 1e-14
+
+
+def test_v_gauge_invariance(sys0):
+    """Multiplying each eigenvector by an arbitrary phase leaves |V|² unchanged."""
+    c, p2, p3, p4 = sys0
+    mesh = (3, 3, 3)
+    base = oracle.harmonic(c, p2, mesh)
+    rng = np.random.default_rng(5)
+    ph = np.exp(2j * np.pi * rng.random((27, 1, 6)))
+    m2 = oracle.Modes(base.omega, base.vel, base.evec * ph, base.eig)
+    A = oracle.Problem(c, p2, p3, p4, mesh, modes=base)
+    B = oracle.Problem(c, p2, p3, p4, mesh, modes=m2)
+    nb = 6
+    for ms in [(4 * nb + 3, 2 * nb + 1, 6 * nb + 4), (10 * nb + 5, 8 * nb + 3, 18 * nb + 4)]:
+        assert abs(abs(A.v3(1, *ms)) ** 2 - abs(B.v3(1, *ms)) ** 2) < 1e-13 * abs(A.v3(1, *ms)) ** 2 + 1e-20
+    ms4 = (4 * nb + 3, 2 * nb + 1, 6 * nb + 4, 12 * nb + 5)
+    assert abs(abs(A.v4(1, -1, *ms4)) ** 2 - abs(B.v4(1, -1, *ms4)) ** 2) < 1e-12 * abs(A.v4(1, -1, *ms4)) ** 2
+
+
+# ------------------------------------------------------------------------------ enumeration
+
+def _brute_force_words(P, ch, m0):
+    """Unpruned enumeration: every partner tuple; momentum closure found by searching all q
+    for the one whose Cartesian vector matches q + s1 q' (+ s2 q'') modulo a reciprocal vector."""
+    nb, N = P.nb, P.nq
+    B = oracle.reciprocal(P.crystal.lattice)
+    qs = oracle.q_cart(P.crystal.lattice, P.mesh)
+    Binv = np.linalg.inv(B)
+
+    def same_mod_G(a, b):
+        f = (a - b) @ Binv
+        return np.all(np.abs(f - np.round(f)) < 1e-9)
+
+    s1 = [1, -1, 1, 1, -1][ch]
+    s2 = [0, 0, 1, -1, -1][ch]
+    q0, j0 = divmod(m0, nb)
+    w = P.modes.omega
+    sig2 = 2.0 * P.sigma * oracle.SIGMA_THZ_TO_RADPS
+    excl = lambda q, j: q == 0 and j < 3
+    out = []
+    if excl(q0, j0):
+        return np.zeros(0, np.uint64)
+    for q1 in range(N):
+        if ch < 2:
+            target = qs[q0] + s1 * qs[q1]
+            q2 = [k for k in range(N) if same_mod_G(qs[k], target)][0]
+            for j1 in range(nb):
+                for j2 in range(nb):
+                    if excl(q1, j1) or excl(q2, j2):
+                        continue
+                    d = oracle.delta(ch, w[m0], w[q1 * nb + j1], w[q2 * nb + j2])
+                    if abs(d) <= sig2:
+                        out.append((q1 * nb + j1) * nb + j2)
+        else:
+            for j1 in range(nb):
+                for q2 in range(N):
+                    target = qs[q0] + s1 * qs[q1] + s2 * qs[q2]
+                    q3 = [k for k in range(N) if same_mod_G(qs[k], target)][0]
+                    for j2 in range(nb):
+                        for j3 in range(nb):
+                            if excl(q1, j1) or excl(q2, j2) or excl(q3, j3):
+                                continue
+                            d = oracle.delta(ch, w[m0], w[q1 * nb + j1], w[q2 * nb + j2], w[q3 * nb + j3])
+                            if abs(d) <= sig2:
+                                out.append((((q1 * nb + j1) * N + q2) * nb + j2) * nb + j3)
+    return np.array(out, np.uint64)
+
+
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 2, 2)])
+def test_enumeration_matches_brute_force(sys0, mesh):
+    P = oracle.Problem(*sys0, mesh)
+    rng = np.random.default_rng(0)
+    nm = P.nq * P.nb
+    for m0 in sorted(set(rng.integers(0, nm, size=4).tolist()) | {nm - 1}):
+        for ch in range(5):
+            a = P.processes(ch, m0)
+            b = _brute_force_words(P, ch, m0)
+            assert a.dtype == np.uint64 and np.array_equal(a, b), (ch, m0)
+
+
+def test_enumeration_matches_brute_force_3ph_3cubed(prob3):
+    P = prob3
+    for m0 in [4, 17, 40, 161]:
+        for ch in (0, 1):
+            assert np.array_equal(P.processes(ch, m0), _brute_force_words(P, ch, m0))
+
+
+def test_partner_swap_symmetry(prob3):
+    """With fixed σ and the symmetric Δ forms: the ++ list is closed under (λ' <-> λ''), +- under
+    (λ'' <-> λ''') and -- under every permutation of the three partners."""
+    P = prob3
+    nb, N = P.nb, P.nq
+    for m0 in [10, 33, 77]:
+        for ch, perms in [(2, [(1, 0, 2)]), (3, [(0, 2, 1)]), (4, list(itertools.permutations(range(3))))]:
+            words = P.processes(ch, m0)
+            q0 = m0 // nb
+            s1, s2 = [(1, 1), (1, -1), (-1, -1)][ch - 2]
+            tuples = set()
+            for wd in words.tolist():
+                q1, j1, q2, j2, j3 = oracle.decode4(wd, nb, N)
+                q3c = (oracle.q_coords(P.mesh)[q0] + s1 * oracle.q_coords(P.mesh)[q1] + s2 * oracle.q_coords(P.mesh)[q2]) % 3
+                q3 = int(q3c[0] + 3 * (q3c[1] + 3 * q3c[2]))
+                tuples.add(((q1, j1), (q2, j2), (q3, j3)))
+            for perm in perms:
+                for t in tuples:
+                    assert tuple(t[i] for i in perm) in tuples
+
+
+def test_occupation_factors_on_shell():
+    """On shell the forward-minus-backward occupation factors equal the RTA forms
+    (equilibrium forward rate)/(n (n+1)) x n: n'(1+n'')/(1+n) etc."""
+    rng = np.random.default_rng(3)
+    x = lambda w: 1.0 / math.expm1(w)          # ħω/kT = w
+    for _ in range(50):
+        a, b, c = rng.uniform(0.05, 3.0, size=3)
+        # 3ph+: λ + λ' -> λ'' ; ω'' = ω + ω'
+        n, n1, n2 = x(a), x(b), x(a + b)
+        assert abs(oracle.occupation_factor(0, n1, n2) - n1 * (1 + n2) / (1 + n)) < 1e-12 * (1 + n1)
+        # 3ph-: λ -> λ' + λ'' ; ω = ω' + ω''
+        n, n1, n2 = x(b + c), x(b), x(c)
+        assert abs(oracle.occupation_factor(1, n1, n2) - (1 + n1) * (1 + n2) / (1 + n)) < 1e-12 * (1 + n1 * n2)
+        # 4ph++: λ + λ' + λ'' -> λ''' ; ω''' = ω + ω' + ω''
+        n, n1, n2, n3 = x(a), x(b), x(c), x(a + b + c)
+        ref = n1 * n2 * (1 + n3) / (1 + n)
+        assert abs(oracle.occupation_factor(2, n1, n2, n3) - ref) < 1e-10 * (1 + abs(ref))
+        # 4ph+-: λ + λ' -> λ'' + λ''' ; ω''' = ω + ω' - ω''
+        if a + b > c:
+            n, n1, n2, n3 = x(a), x(b), x(c), x(a + b - c)
+            ref = n1 * (1 + n2) * (1 + n3) / (1 + n)
+            assert abs(oracle.occupation_factor(3, n1, n2, n3) - ref) < 1e-10 * (1 + abs(ref))
+        # 4ph--: λ -> λ' + λ'' + λ''' ; ω = ω' + ω'' + ω'''
+        n, n1, n2, n3 = x(a + b + c), x(a), x(b), x(c)
+        ref = (1 + n1) * (1 + n2) * (1 + n3) / (1 + n)
+        assert abs(oracle.occupation_factor(4, n1, n2, n3) - ref) < 1e-10 * (1 + abs(ref))
+
+
+def test_delta_swap_bit_symmetric():
+    """The canonical Δ forms are bit-identical under the partner swaps they must respect."""
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        w, a, b, c = rng.uniform(0.1, 90.0, size=4)
+        assert oracle.delta(2, w, a, b, c) == oracle.delta(2, w, b, a, c)
+        assert oracle.delta(3, w, a, b, c) == oracle.delta(3, w, a, c, b)
+        for p in itertools.permutations((a, b, c)):
+            assert oracle.delta(4, w, *p) == oracle.delta(4, w, a, b, c)
+
+
+def test_weighted_phase_space_3ph_brute_force(prob3):
+    """WP3+ = (1/N) Σ (n'-n'') δ / (ω ω' ω'') over the brute-force kept set (Alg. 1)."""
+    P = prob3
+    nb, N = P.nb, P.nq
+    occ = oracle.occupations(P.modes.omega, P.T)
+    w = P.modes.omega
+    sig = P.sigma * oracle.SIGMA_THZ_TO_RADPS
+    modes = [8, 25, 50]
+    _, wp, _ = P.rates(modes, channel_mask=1)
+    for i, m0 in enumerate(modes):
+        tot = 0.0
+        for wd in _brute_force_words(P, 0, m0).tolist():
+            q1, j1, j2 = oracle.decode3(wd, nb)
+            qc = oracle.q_coords(P.mesh)
+            q2c = (qc[m0 // nb] + qc[q1]) % 3
+            m1, m2 = q1 * nb + j1, int(q2c[0] + 3 * (q2c[1] + 3 * q2c[2])) * nb + j2
+            d = w[m0] + w[m1] - w[m2]
+            tot += (occ[m1] - occ[m2]) * math.exp(-d * d / sig ** 2) / (sig * math.sqrt(math.pi) * w[m0] * w[m1] * w[m2])
+        assert abs(wp[0, i] - tot / N) < 1e-12 * abs(tot / N)
+
+
+# ------------------------------------------------------------------------------ rates
+
+def test_band_folding_equivalence():
+    """The primitive cell on a 2x2x4 mesh and its 1x1x2 supercell on a 2x2x2 mesh describe the
+    same crystal: every channel's Γ, summed over degenerate groups, agrees.  This pins the 1/N and
+    1/N² normalisations, the mass factors and the multi-atom cluster handling."""
+    base = diamond_crystal()
+    sc = supercell_crystal(base, 2)
+    pp = oracle.Problem(base, *morse_ifcs(base, seed=0, perturb=0.0), (2, 2, 4))
+    ps = oracle.Problem(sc, *morse_ifcs(sc, seed=0, perturb=0.0), (2, 2, 2))
+    qS = [1, 5]                                       # supercell q indices checked
+    for iqS in qS:
+        cS = oracle.q_coords((2, 2, 2))[iqS]
+        # primitive q's folding onto it: i3_P = i3_S and i3_S + 2
+        prim = [int(cS[0] + 2 * (cS[1] + 2 * i3)) for i3 in (cS[2], cS[2] + 2)]
+        mS = [iqS * 12 + j for j in range(12)]
+        mP = [q * 6 + j for q in prim for j in range(6)]
+        gS, _, _ = ps.rates(mS)
+        gP, _, _ = pp.rates(mP)
+        wS = ps.modes.omega[mS]
+        wP = pp.modes.omega[mP]
+        oS, oP = np.argsort(wS, kind="stable"), np.argsort(wP, kind="stable")
+        assert np.allclose(wS[oS], wP[oP], rtol=1e-10)
+        ws = wS[oS]
+        groups = np.split(np.arange(12), np.where(np.diff(ws) > 1e-6 * ws.max())[0] + 1)
+        for ch in range(5):
+            floor = 1e-12 * np.abs(gP[ch]).max()      # channels that vanish by symmetry
+            for g in groups:
+                a = gS[ch][oS][g].sum()
+                b = gP[ch][oP][g].sum()
+                assert abs(a - b) <= 1e-9 * max(abs(a), abs(b)) + floor, (ch, g, a, b)
+
+
+def test_gamma_nonnegative_for_hard_modes(prob3):
+    """Γ >= 0 for every mode with ω >= 2σ (off-shell Gaussian tails can make softer modes negative)."""
+    P = prob3
+    modes = np.arange(3, P.nq * P.nb, 7)
+    g, wp, cnt = P.rates(modes, channel_mask=0b11)
+    hard = P.modes.omega[modes] >= 2 * P.sigma * oracle.SIGMA_THZ_TO_RADPS
+    assert np.all(g[:2, hard] >= 0.0)
+    assert np.all(cnt >= 0)
+
+
+def test_excluded_modes_are_zero(prob3):
+    g, wp, cnt = prob3.rates([0, 1, 2])
+    assert np.all(g == 0) and np.all(wp == 0) and np.all(cnt == 0)
+
+
+def test_kappa_isotropic_unperturbed(sys_clean):
+    """The unperturbed crystal on a Γ-centred cubic-symmetric mesh gives κ ∝ I (3ph, RTA)."""
+    P = oracle.Problem(*sys_clean, (4, 4, 4))
+    g, _, _ = P.rates(channel_mask=0b11)
+    k = P.kappa(g[0] + g[1])
+    assert k[0, 0] > 0
+    assert np.allclose(np.diag(k), k[0, 0], rtol=1e-6)
+    assert np.abs(k - np.diag(np.diag(k))).max() < 1e-6 * k[0, 0]
+
+
+# ------------------------------------------------------------------------------ gradient
+
+@pytest.fixture(scope="module")
+def prob2(sys0):
+    return oracle.Problem(*sys0, (2, 2, 2))
+
+
+def test_gradient_euler_identity(prob2):
+    """Γ is a quadratic form in Φ3 (3ph) and in Φ4 (4ph) at fixed modes: Σ Φ ∂Γ/∂Φ = 2Γ."""
+    P = prob2
+    modes = [4, 9, 23, 40]
+    g, _, _ = P.rates(modes)
+    rng = np.random.default_rng(0)
+    dL = rng.standard_normal((5, len(modes)))
+    L3 = float(np.sum(dL[:2] * g[:2]))
+    L4 = float(np.sum(dL[2:] * g[2:]))
+    g3, g4 = P.grad(modes, dL)
+    assert abs(np.sum(P.phi3.phi * g3) - 2 * L3) < 1e-10 * abs(L3)
+    assert abs(np.sum(P.phi4.phi * g4) - 2 * L4) < 1e-10 * abs(L4)
+
+
+def test_gradient_central_differences(prob2):
+    """Central differences of L along single cluster entries (exact for a quadratic up to rounding)."""
+    P = prob2
+    modes = [7, 22]
+    rng = np.random.default_rng(1)
+    dL = rng.standard_normal((5, len(modes)))
+    g3, g4 = P.grad(modes, dL)
+    for (order, c, k) in [(3, 5, 13), (3, 40, 2), (4, 3, 40), (4, 100, 7), (4, 200, 80)]:
+        ifc = (P.phi3 if order == 3 else P.phi4)
+        h = 1e-3 * max(abs(ifc.phi[c, k]), 1.0)
+        vals = []
+        for s in (+1, -1):
+            mod = ifc.copy()
+            mod.phi[c, k] += s * h
+            Q = P.with_anharmonic(phi3=mod) if order == 3 else P.with_anharmonic(phi4=mod)
+            gg, _, _ = Q.rates(modes)
+            part = slice(0, 2) if order == 3 else slice(2, 5)      # Φ3 enters 3ph only, Φ4 4ph only
+            vals.append(float(np.sum(dL[part] * gg[part])))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = (g3 if order == 3 else g4)[c, k]
+        gref = np.abs(g3 if order == 3 else g4).max()
+        assert abs(fd - an) < 1e-7 * max(abs(an), 1e-3 * gref), (order, c, k, fd, an)
+
+
+def test_gamma_scales_quadratically(prob2):
+    modes = [5, 30]
+    g, _, _ = prob2.rates(modes)
+    p4 = prob2.phi4.copy()
+    p4.phi *= 1.7
+    g2, _, _ = prob2.with_anharmonic(phi4=p4).rates(modes)
+    assert np.allclose(g2[2:], 1.7 ** 2 * g[2:], rtol=1e-13)
+    assert np.array_equal(g2[:2], g[:2])

@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of the three- and four-phonon scattering-rate path on GB300.
+
+One step = one pass of the hot path over the workload: the 3ph and 4ph rates Γ of every mode
+(enumeration, energy window, matrix elements, weights, reduction; fc4_rates with all five
+channels) followed by the RTA conductivity κ (fc4_kappa), inputs resident in HBM.  The metric
+is kept four-phonon processes per second.  The end-to-end figure ("e2e") times the same work
+through the C interface from host buffers: fc4_init (host-to-device copy of the crystal and
+clusters, device harmonic solve, phase tables), fc4_rates, fc4_kappa, the device-to-host copy
+of Γ, WP, counts and κ, and fc4_destroy.
+
+Workload: two-atom Morse diamond crystal (a = 5.43 Å, m = 28.0855 amu, D = 2 eV, α = 1.5/Å,
+r0 = 2.35 Å, seeded 1 % bond perturbations), Γ-centred 8x8x8 mesh (512 q, 3072 modes),
+T = 300 K, fixed Gaussian σ = 0.1 THz.  Synthetic: no first-principles force constants.
+
+--impl reference times the FP64 CPU oracle (the test reference) on the same workload, on a
+bounded sample of modes and partners per step, on the host's cores.
+
+Multi-GPU (torchrun): each rank computes an independent crystal (seed = rank) of the same size;
+no data-path collective ("weak" scaling); the max step time over ranks is reported.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4ph processes/s on 1 GB300, mixed vs FP64 GPU at κ rel err ≤1e-4; % of roofline"
+UNIT = "processes/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fc4", choices=["fc4", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--mesh", type=int, default=8)
+    p.add_argument("--T", type=float, default=300.0)
+    p.add_argument("--sigma", type=float, default=0.1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-qp", type=int, default=24, help="oracle sample: partners q' < cpu_qp")
+    p.add_argument("--cpu-q", type=int, default=2, help="oracle sample: q points (x nb modes)")
+    p.add_argument("--block-threads", type=int, default=0)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(args, seed):
+    from synth import morse_system
+    return morse_system(seed=seed), (args.mesh,) * 3
+
+
+def config_of(args, precision):
+    n = args.mesh
+    return {"workload": f"morse-diamond-2atom-{n}x{n}x{n}-all-modes", "mesh": [n, n, n], "n_q": n ** 3,
+            "nb": 6, "T_K": args.T, "sigma_THz": args.sigma, "channels": "3ph+,3ph-,4ph++,4ph+-,4ph--",
+            "precision": precision, "step": "fc4_rates(all modes, 5 channels) + fc4_kappa",
+            "l2": "flushed between steps (512 MiB write)"}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_sample(args, seed=0, qp=None, nq=None):
+    """Oracle on a bounded sample of the same workload: cpu_q q points (all branches) and
+    partners q' < cpu_qp; returns (kept 4ph processes, seconds, sample description, threads)."""
+    import oracle
+    from synth.sampling import sample_q
+    sysm, mesh = workload(args, seed)
+    prob = oracle.Problem(*sysm, mesh, T=args.T, sigma=args.sigma)
+    qs = sample_q(int(np.prod(mesh)), nq or args.cpu_q, seed=0)
+    modes = np.array([q * 6 + j for q in qs for j in range(6)], np.int32)
+    qp = qp or args.cpu_qp
+    t0 = time.perf_counter()
+    _, _, cnt = prob.rates(modes, channel_mask=0b11100, qp_limit=qp)
+    dt = time.perf_counter() - t0
+    kept = int(cnt[2:].sum())
+    desc = (f"oracle (C, FP64, OpenMP) on {modes.size} modes (q = {qs.tolist()}, all branches), "
+            f"4ph channels, partners q' < {qp} of {int(np.prod(mesh))}; {kept} kept processes")
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return kept, dt, desc, threads
+
+
+def clocks_start():
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                 else os.devnull, "w")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(p, f, gpu_index):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except Exception:
+        p.kill()
+        out, _ = p.communicate()
+    rows = []
+    for line in out.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            if int(parts[0]) != gpu_index:
+                continue
+            rows.append(parts)
+        except ValueError:
+            continue
+    if f:
+        f.write(out)
+        f.close()
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows]
+    mx = max(float(r[2]) for r in rows)
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        for n, v in zip(names, r[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def flops_alg(stats, info, nb):
+    """Algorithmic FP32 flops of the four-phonon kernel per channel (the factored contraction):
+    window 2 per candidate; W 9 * 46 per cluster per (λ, q', j'); Y 90 per key per item;
+    V 8 * nb + weight 24 per kept process (complex multiply-add = 8 flops)."""
+    nc4, nk = info["nc4"], info["n_keys"]
+    out = []
+    for ch in range(5):
+        if ch < 2:
+            out.append(0.0)
+            continue
+        cand = stats["candidates"][ch]
+        units_j = cand / (info["N"] * nb * nb)          # (λ, q', j') units
+        out.append(2.0 * cand + units_j * nc4 * 9 * 46 + stats["items"][ch] * nk * 90.0
+                   + stats["kept"][ch] * (8.0 * nb + 24.0))
+    return out
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2510_00518_gb300 import Engine, FP64, MIXED
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = MIXED if args.precision == "mixed" else FP64
+    sysm, mesh = workload(args, seed=rank)
+    eng = Engine(*sysm, mesh, precision=prec, block_threads=args.block_threads, timing=True)
+    info = eng.info()
+    nb = info["nb"]
+    nm = info["N"] * nb
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    g = torch.empty((5, nm), dtype=torch.float64, device=dev)
+    wp = torch.empty_like(g)
+    cnt = torch.empty((5, nm), dtype=torch.int64, device=dev)
+    kap = torch.empty(9, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step():
+        eng.rates(args.T, args.sigma, 31, out=(g, wp, cnt))
+        eng.kappa(args.T, g.sum(0), out=kap)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = eng.stats()
+    kept4 = int(stats["kept"][2:].sum())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    k_ms = []
+    clk_p, clk_f = clocks_start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    launches0 = eng.timings()["launches"]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        k_ms.append(eng.timings())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clocks = clocks_stop(clk_p, clk_f, local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    launches = (k_ms[-1]["launches"] - launches0) if k_ms else 0
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        kk = torch.tensor([kept4], device=dev, dtype=torch.float64)
+        dist.all_reduce(kk)
+        kept_total = float(kk.item())
+    else:
+        kept_total = float(kept4)
+    value = kept_total / (ms * 1e-3)
+
+    # dominant kernel (the 4ph channel with the largest device time) and its roofline
+    chans = ["4ph++", "4ph+-", "4ph--"]
+    avg = {c: float(np.mean([t[c] for t in k_ms])) for c in chans}
+    dom = max(avg, key=avg.get)
+    ch = 2 + chans.index(dom)
+    fl = flops_alg(stats, info, nb)[ch]
+    import json as _json
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_clock = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if prec == MIXED:
+        peak = 152 * 128 * 2 * 2070e6 / 1e12              # FP32 CUDA-core FLOP/s at max SM clock
+        bound_note = "FP32 FMA issue: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (max clock)"
+    else:
+        peak = 1.25                                         # FP64 (nominal GB300)
+        bound_note = "FP64: nominal 1.25 TFLOP/s"
+    achieved = fl / (avg[dom] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": f"rates4 {dom}", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "launch_ms": avg[dom], "alg_flops_per_launch": fl, "peak_basis": bound_note,
+            "kernel_ms": avg}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32" if prec == MIXED else "f64",
+              "data": "synthetic (seeded Morse diamond crystal)", "config": config_of(args, args.precision),
+              "kept_4ph_per_step": kept4, "candidates_4ph_per_step": int(stats["candidates"][2:].sum()),
+              "wall_s": wall, "gpu_launches": int(launches), "roofline": roof, "clocks": clocks}
+
+    # end to end through the C interface from host buffers
+    if not args.no_e2e:
+        import ctypes
+        import paper_2510_00518_gb300 as pkg
+        c, p2, p3, p4 = sysm
+        gh = np.zeros((5, nm))
+        wph = np.zeros((5, nm))
+        ch_ = np.zeros((5, nm), np.int64)
+        kh = np.zeros(9)
+        h2d = sum(np.asarray(x).nbytes for x in (c.lattice, c.positions, c.masses, p2.atoms, p2.cells,
+                                                 p2.phi, p3.atoms, p3.cells, p3.phi, p4.atoms, p4.cells, p4.phi))
+        d2h = gh.nbytes + wph.nbytes + ch_.nbytes + kh.nbytes
+        e2e_ms = []
+        for i in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e = Engine(*sysm, mesh, precision=prec, block_threads=args.block_threads)
+            g2, wp2, c2 = e.rates(args.T, args.sigma, 31)
+            k2 = e.kappa(args.T, g2.sum(0))
+            gh[:] = g2.cpu().numpy()
+            wph[:] = wp2.cpu().numpy()
+            ch_[:] = c2.cpu().numpy()
+            kh[:] = k2.cpu().numpy().reshape(-1)
+            e.close()
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t1) * 1e3)
+        em = float(np.mean(e2e_ms))
+        result["e2e"] = {"value": kept_total / (em * 1e-3) if world == 1 else kept4 / (em * 1e-3) * world,
+                         "unit": UNIT, "ms_per_step": em, "h2d_bytes_per_step": int(h2d),
+                         "d2h_bytes_per_step": int(d2h)}
+        result["kappa_W_mK"] = kh.reshape(3, 3).tolist()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        kept, dt, desc, thr = cpu_oracle_sample(args)
+        result["cpu_baseline"] = {"value": kept / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                  "sample": desc, "seconds": dt}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# ------------------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args, qp=2, nq=1)
+    kept_tot, secs = 0, 0.0
+    desc, thr = "", 1
+    for _ in range(args.steps):
+        kept, dt, desc, thr = cpu_oracle_sample(args)
+        kept_tot += kept
+        secs += dt
+    v = kept_tot / secs
+    ms = secs / args.steps * 1e3
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Morse diamond crystal)",
+           "config": config_of(args, "fp64-oracle"),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,179 @@
+/*
+ * fc4.h - C interface of libfc4: three- and four-phonon scattering rates Γ(q,j), weighted phase
+ * space, process lists, RTA thermal conductivity and the adjoint with respect to the cubic and
+ * quartic force constants, computed on one GB300 GPU (sm_103a).
+ *
+ * Method: arxiv 2510.00518 (FourPhonon_GPU).  The paper states the problem as: for every mode
+ * (q, j), enumerate the momentum-conserving partners, keep those inside the energy window
+ * |Δ| <= 2σ, and accumulate the weighted phase space and WP * |V|² into Γ (Algorithms 1-4,
+ * Methodology section); κ follows in the relaxation-time approximation (Results section).
+ * The channel conventions, matrix elements, weights and unit constants that the paper leaves
+ * as black boxes are spelled out at each entry point below.
+ *
+ * Conventions shared by every call
+ *   - Units: Å, amu, eV; ω in rad/ps; Γ in ps^-1; κ in W/(m K); T in K.
+ *   - Mesh: Γ-centred n1 x n2 x n3, q index = i1 + n1 (i2 + n2 i3) (first axis fastest),
+ *     q = Σ_k (i_k / n_k) b_k with a_i . b_j = 2π δ_ij.  Mode index = q * nb + j, nb = 3 n_atoms.
+ *   - Channels (bit k of a channel mask selects channel k):
+ *       0 3ph+  q'' = q + q'          Δ = (ω + ω') - ω''
+ *       1 3ph-  q'' = q - q'          Δ = ω - (ω' + ω'')
+ *       2 4ph++ q''' = q + q' + q''   Δ = (ω - ω''') + (ω' + ω'')
+ *       3 4ph+- q''' = q + q' - q''   Δ = (ω + ω') - (ω'' + ω''')
+ *       4 4ph-- q''' = q - q' - q''   Δ = ω - ((s0 + s1) + s2), partner ω in ascending order
+ *     A process is kept iff |Δ| <= 2σ evaluated in IEEE FP64 with exactly these parentheses.
+ *   - The three acoustic modes at Γ (q index 0, branches 0..2) are excluded as the mode and as
+ *     partners (ω = 0).
+ *   - Ownership: the caller owns every buffer it passes.  fc4_init copies its inputs.  Output
+ *     buffers named "device" must be device memory of the current CUDA device, allocated by the
+ *     caller; results are ready when the given stream (cudaStream_t, NULL = legacy default
+ *     stream) reaches the point of the call.  Host pointers are read or written before return.
+ *   - Errors: no call throws.  On any status other than FC4_OK the outputs are unspecified and
+ *     fc4_last_error(ctx) holds a one-line message.  Calls on one context must not overlap.
+ */
+#ifndef FC4_H
+#define FC4_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc4_ctx fc4_ctx;
+
+typedef enum {
+    FC4_OK = 0,
+    FC4_ERR_INVALID = 1,   /* bad argument (size, index, pointer, channel, mesh) */
+    FC4_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    FC4_ERR_OOM = 3,       /* device allocation failed */
+    FC4_ERR_TIMEOUT = 4,   /* a bounded device wait expired */
+    FC4_ERR_UNSTABLE = 5,  /* harmonic eigenvalue below -1e-8 eV/(Å² amu) (imaginary mode) */
+    FC4_ERR_STATE = 6      /* call order violated (e.g. backward before rates) */
+} fc4_status;
+
+/* Arithmetic of the matrix-element contraction.  The energy window, the process counts and the
+ * final reduction into Γ are FP64 in every mode. */
+typedef enum {
+    FC4_FP64 = 0,          /* FP64 contraction and FP64 weights (reference-accurate) */
+    FC4_MIXED = 1          /* FP32 contraction and FP32 weights, FP64 window and accumulation */
+} fc4_precision;
+
+typedef struct {
+    int n_atoms;
+    double lattice[9];        /* rows a1, a2, a3 (Å) */
+    const double *positions;  /* [n_atoms][3] Cartesian Å (host) */
+    const double *masses;     /* [n_atoms] amu (host) */
+} fc4_crystal;
+
+/* Force-constant clusters of one order (2, 3 or 4); leg 0 sits in the home cell. */
+typedef struct {
+    int order;
+    int n_clusters;
+    const int *atoms;         /* [n_clusters][order] basis-atom index per leg (host) */
+    const int *cells;         /* [n_clusters][order-1][3] lattice coordinates of legs 1.. (host) */
+    const double *phi;        /* [n_clusters][3^order] eV/Å^order, last Cartesian index fastest (host) */
+} fc4_ifc;
+
+typedef struct {
+    int precision;            /* fc4_precision */
+    int block_threads;        /* threads per block of the 4ph kernel; 0 = default (128) */
+    long long timeout_cycles; /* bound of device-side waits; 0 = default */
+    int timing;               /* 1: record CUDA events around every kernel launch (fc4_timings) */
+    int allow_unstable;       /* 1: fc4_init keeps a crystal with imaginary modes (ω set to 0 for them) */
+    int reserved[2];
+} fc4_options;
+
+/* fc4_init - build a context: copy the crystal, the clusters and the mesh to the device, solve
+ * the harmonic problem on the device (batched FP64 Jacobi eigensolver of the dynamical matrix
+ * D(q) = Σ_R Φ2(0a, Rb) exp(i q.R) / sqrt(m_a m_b), Hermitised; ω = sqrt(λ); group velocities
+ * by Hellmann-Feynman), and build the phase tables exp(i q.R) of every cluster cell vector.
+ * phi2 is required; phi3 / phi4 may have n_clusters = 0.  opt may be NULL (FP64 defaults).
+ * Paper: harmonic properties are an input of Algorithm 1 (ω, v, e of every mode).
+ * Returns FC4_ERR_UNSTABLE if an eigenvalue other than the Γ acoustic ones is below -1e-8. */
+fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_ifc *phi3,
+                    const fc4_ifc *phi4, const int mesh[3], const fc4_options *opt,
+                    fc4_ctx **out);
+
+/* fc4_set_modes - replace the harmonic modes (host arrays): omega [N*nb] rad/ps, vel [N*nb][3]
+ * Å/ps, evec [N][nb component][nb branch][2] (re, im).  Used to evaluate the rates for modes
+ * computed elsewhere (e.g. to compare against a reference with the same eigenvector gauge). */
+fc4_status fc4_set_modes(fc4_ctx *ctx, const double *omega, const double *vel, const double *evec);
+
+/* fc4_get_modes - copy the current modes to host arrays (same layouts; any pointer may be NULL). */
+fc4_status fc4_get_modes(fc4_ctx *ctx, double *omega, double *vel, double *evec);
+
+/* fc4_rates - Γ, WP and kept-process counts of every mode (q, j) of the q points in q_subset.
+ *
+ *   Γ3(λ) = C3/N  Σ w |V3|²,  Γ4(λ) = C4/N² Σ w |V4|²,  WP3 = Σ w / N,  WP4 = Σ w / N²
+ *   w = sym * F * exp(-Δ²/σ²) / (σ sqrt(π)) / (ω ω' ω'' [ω'''])          (Algorithm 1, WP)
+ *   sym = 1, 1/2, 1/2, 1/2, 1/6 for channels 0..4;  F = n' - n'', 1 + n' + n'',
+ *   n'n''(1+n''') - (1+n')(1+n'')n''', n'(1+n'')(1+n''') - (1+n')n''n''',
+ *   (1+n')(1+n'')(1+n''') - n'n''n''' (n = Bose-Einstein occupation at T);
+ *   V3 = Σ_c Σ Φ_c e_λ e^±_λ' e*_λ'' exp(i(±q'.R1 - q''.R2)) / sqrt(m m m)
+ *   V4 = Σ_c Σ Φ_c e_λ e^s1_λ' e^s2_λ'' e*_λ''' exp(i(s1 q'.R1 + s2 q''.R2 - q'''.R3)) / sqrt(m m m m)
+ *   (e^+ = e, e^- = conj(e); C3 = ħπ/4, C4 = ħ²π/8 converted to ps^-1.)
+ *
+ * T_K > 0.  sigma_adaptive = 0: fixed Gaussian width sigma_value in THz (σ = 2π sigma_value
+ * rad/ps).  Adaptive widths are not supported by this entry point (FC4_ERR_INVALID).
+ * q_subset: host array of n_q distinct q indices (NULL = all N q points, n_q ignored).
+ * gamma_out, wp_out: device [5][n_q*nb] doubles; counts_out: device [5][n_q*nb] long long;
+ * wp_out and counts_out may be NULL.  Channels outside channel_mask are written as 0.
+ * The call records (T, σ, mask, subset) for fc4_rates_backward. */
+fc4_status fc4_rates(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_value,
+                     int channel_mask, const int *q_subset, int n_q, double *gamma_out,
+                     double *wp_out, long long *counts_out, void *stream);
+
+/* fc4_processes - the kept processes of one mode and channel, as canonical 64-bit words in
+ * ascending order (the paper's loop order q', j', then the remaining branches; Algorithm 3):
+ *   3ph: word = (q' nb + j') nb + j''
+ *   4ph: word = (((q' nb + j') N + q'') nb + j'') nb + j'''
+ * words: host array of capacity cap (may be NULL when cap = 0); *n_out receives the count even
+ * when it exceeds cap (then only the first cap words are written).  Uses the (T, σ) of the last
+ * fc4_rates call, or 300 K and 0.1 THz before any. */
+fc4_status fc4_processes(fc4_ctx *ctx, int channel, int mode, unsigned long long *words,
+                         long long cap, long long *n_out);
+
+/* fc4_kappa - RTA thermal conductivity κ_αβ = 1/(N V_cell) Σ_λ C_λ v_α v_β / Γ_λ (W/(m K)),
+ * C_λ = k_B x² n (n + 1), x = ħω / k_B T, over every mode of the mesh with ω > 0 and Γ_λ > 0.
+ * gamma_total: device [N*nb] total scattering rate per mode (ps^-1); kappa_out: device [9]. */
+fc4_status fc4_kappa(fc4_ctx *ctx, double T_K, const double *gamma_total, double *kappa_out,
+                     void *stream);
+
+/* fc4_rates_backward - gradient of L = Σ_{ch,i} dL_dgamma[ch][i] Γ_ch(i) with respect to every
+ * stored Φ3 and Φ4 entry (entries independent), at fixed modes and σ, for the (T, σ, mask,
+ * subset) of the last fc4_rates call:
+ *   dL/dΦ_c = Σ_processes g w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
+ * dL_dgamma: device [5][n_q*nb]; dphi3: device [nc3][27]; dphi4: device [nc4][81] (overwritten;
+ * either may be NULL to skip that order).  Returns FC4_ERR_STATE before any fc4_rates call. */
+fc4_status fc4_rates_backward(fc4_ctx *ctx, const double *dL_dgamma, double *dphi3,
+                              double *dphi4, void *stream);
+
+/* fc4_update_anharmonic - replace the Φ3 and/or Φ4 values (host, same cluster lists and layout
+ * as fc4_init; NULL keeps the current values).  Modes and phase tables are unchanged. */
+fc4_status fc4_update_anharmonic(fc4_ctx *ctx, const double *phi3, const double *phi4);
+
+/* fc4_stats - work counters of the last fc4_rates call (synchronises the device):
+ * out[3*ch + 0] = kept processes, out[3*ch + 1] = four-phonon (q'', j''') items evaluated (0 for
+ * 3ph), out[3*ch + 2] = candidate tuples before the window, for channels ch = 0..4. */
+fc4_status fc4_stats(fc4_ctx *ctx, long long out[15]);
+
+/* fc4_timings - device time in ms of the kernels launched by the last fc4_rates / fc4_kappa
+ * calls, measured with CUDA events recorded on the launching stream around each launch (needs
+ * fc4_options.timing = 1; synchronises on those events): out[0..4] the rate kernel of channel
+ * 0..4 (0 if not launched), out[5] the reduction, out[6] the conductivity, out[7] the occupation
+ * table, out[8] the number of kernels libfc4 launched since the context was created. */
+fc4_status fc4_timings(fc4_ctx *ctx, double out[9]);
+
+/* fc4_info - sizes of a context: out[0..7] = n_atoms, nb, N, nc2, nc3, nc4, n_keys, precision. */
+fc4_status fc4_info(const fc4_ctx *ctx, long long out[8]);
+
+/* fc4_last_error - message of the last failed call on ctx (or of the last failed fc4_init when
+ * ctx is NULL).  The string lives until the next call on ctx. */
+const char *fc4_last_error(const fc4_ctx *ctx);
+
+/* fc4_destroy - free every device and host resource of ctx (NULL is a no-op). */
+void fc4_destroy(fc4_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC4_H */

@@ -1,0 +1,267 @@
+"""Python binding of libfc4 (three- and four-phonon scattering rates on one GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels behind the
+C interface declared in ``include/fc4.h``.  PyTorch provides device memory and the current
+stream.  There is no CPU fallback: importing the binding fails if ``libfc4.so`` cannot be
+loaded, and every entry point raises ``FC4Error`` on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "CHANNELS", "lib_path"]
+
+FP64, MIXED = 0, 1
+CHANNELS = ("3ph+", "3ph-", "4ph++", "4ph+-", "4ph--")
+STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "UNSTABLE", 6: "STATE"}
+
+
+class FC4Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fc4 status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class _Crystal(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("lattice", ctypes.c_double * 9),
+                ("positions", ctypes.c_void_p), ("masses", ctypes.c_void_p)]
+
+
+class _IFC(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("n_clusters", ctypes.c_int), ("atoms", ctypes.c_void_p),
+                ("cells", ctypes.c_void_p), ("phi", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("timeout_cycles", ctypes.c_longlong), ("timing", ctypes.c_int),
+                ("allow_unstable", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libfc4.so (built in-tree by ``build.py``); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libfc4.so not found at {path}; run paper_2510_00518_gb300/build.py")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "fc4_init": [ctypes.POINTER(_Crystal), ctypes.POINTER(_IFC), ctypes.POINTER(_IFC),
+                     ctypes.POINTER(_IFC), vp, ctypes.POINTER(_Options), ctypes.POINTER(vp)],
+        "fc4_set_modes": [vp, vp, vp, vp],
+        "fc4_get_modes": [vp, vp, vp, vp],
+        "fc4_rates": [vp, d, i, d, i, vp, i, vp, vp, vp, vp],
+        "fc4_processes": [vp, i, i, vp, ll, ctypes.POINTER(ll)],
+        "fc4_kappa": [vp, d, vp, vp, vp],
+        "fc4_rates_backward": [vp, vp, vp, vp, vp],
+        "fc4_update_anharmonic": [vp, vp, vp],
+        "fc4_info": [vp, vp],
+        "fc4_stats": [vp, vp],
+        "fc4_timings": [vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fc4_last_error.argtypes = [vp]
+    lib.fc4_last_error.restype = ctypes.c_char_p
+    lib.fc4_destroy.argtypes = [vp]
+    lib.fc4_destroy.restype = None
+    _LIB = lib
+    return lib
+
+
+def _np(x, dt):
+    return np.ascontiguousarray(np.asarray(x), dtype=dt)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Engine:
+    """One fc4 context: a crystal, its Φ2/Φ3/Φ4 clusters and a Γ-centred mesh on the device.
+
+    ``crystal`` needs ``lattice`` (3x3, rows a_i, Å), ``positions`` (n x 3 Å) and ``masses``
+    (amu); each cluster set needs ``order``, ``atoms``, ``cells`` and ``phi`` in the layout of
+    ``include/fc4.h``."""
+
+    def __init__(self, crystal, phi2, phi3, phi4, mesh, precision: int = FP64, block_threads: int = 0,
+                 timing: bool = False, allow_unstable: bool = False):
+        self.lib = load()
+        self.mesh = tuple(int(x) for x in mesh)
+        self.nq = int(np.prod(self.mesh))
+        self.n_atoms = int(np.asarray(crystal.masses).size)
+        self.nb = 3 * self.n_atoms
+        keep = []
+
+        def arr(x, dt):
+            a = _np(x, dt)
+            keep.append(a)
+            return a
+
+        c = _Crystal()
+        c.n_atoms = self.n_atoms
+        c.lattice = (ctypes.c_double * 9)(*_np(crystal.lattice, np.float64).reshape(-1))
+        c.positions = _ptr(arr(crystal.positions, np.float64))
+        c.masses = _ptr(arr(crystal.masses, np.float64))
+
+        def ifc(f, order):
+            s = _IFC()
+            s.order = order
+            if f is None:
+                s.n_clusters = 0
+                return s
+            s.n_clusters = int(np.asarray(f.atoms).shape[0])
+            s.atoms = _ptr(arr(f.atoms, np.int32))
+            s.cells = _ptr(arr(f.cells, np.int32))
+            s.phi = _ptr(arr(f.phi, np.float64))
+            return s
+
+        i2, i3, i4 = ifc(phi2, 2), ifc(phi3, 3), ifc(phi4, 4)
+        self.nc3 = i3.n_clusters
+        self.nc4 = i4.n_clusters
+        opt = _Options()
+        opt.precision = int(precision)
+        opt.block_threads = int(block_threads)
+        opt.timing = int(bool(timing))
+        opt.allow_unstable = int(bool(allow_unstable))
+        m = (ctypes.c_int * 3)(*self.mesh)
+        ctx = ctypes.c_void_p()
+        st = self.lib.fc4_init(ctypes.byref(c), ctypes.byref(i2), ctypes.byref(i3), ctypes.byref(i4),
+                               ctypes.cast(m, ctypes.c_void_p), ctypes.byref(opt), ctypes.byref(ctx))
+        if st != 0:
+            raise FC4Error(st, self.lib.fc4_last_error(None).decode())
+        self.ctx = ctx
+        self.precision = int(precision)
+
+    # -- lifecycle -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fc4_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise FC4Error(st, self.lib.fc4_last_error(self.ctx).decode())
+
+    def info(self) -> dict:
+        out = np.zeros(8, np.int64)
+        self._check(self.lib.fc4_info(self.ctx, _ptr(out)))
+        keys = ("n_atoms", "nb", "N", "nc2", "nc3", "nc4", "n_keys", "precision")
+        return dict(zip(keys, out.tolist()))
+
+    def stats(self) -> dict:
+        """Work counters of the last rates call: kept processes, 4ph items and candidates per
+        channel (synchronises the device)."""
+        out = np.zeros(15, np.int64)
+        self._check(self.lib.fc4_stats(self.ctx, _ptr(out)))
+        o = out.reshape(5, 3)
+        return {"kept": o[:, 0].copy(), "items": o[:, 1].copy(), "candidates": o[:, 2].copy()}
+
+    def timings(self) -> dict:
+        """Per-kernel device times (ms) of the last rates / kappa calls and the launch count."""
+        out = np.zeros(9)
+        self._check(self.lib.fc4_timings(self.ctx, _ptr(out)))
+        names = list(CHANNELS) + ["reduce", "kappa", "occupations"]
+        d = dict(zip(names, out[:8].tolist()))
+        d["launches"] = int(out[8])
+        return d
+
+    # -- modes -------------------------------------------------------------------------------
+    def set_modes(self, omega, vel, evec):
+        om = _np(omega, np.float64)
+        v = _np(vel, np.float64)
+        e = _np(np.asarray(evec, np.complex128), np.complex128).view(np.float64)
+        self._check(self.lib.fc4_set_modes(self.ctx, _ptr(om), _ptr(v), _ptr(e)))
+
+    def get_modes(self):
+        nm = self.nq * self.nb
+        om = np.zeros(nm)
+        v = np.zeros((nm, 3))
+        e = np.zeros((self.nq, self.nb, self.nb), np.complex128)
+        self._check(self.lib.fc4_get_modes(self.ctx, _ptr(om), _ptr(v), _ptr(e.view(np.float64))))
+        return om, v, e
+
+    # -- rates -------------------------------------------------------------------------------
+    def rates(self, T: float, sigma_thz: float, channel_mask: int = 31, q_subset=None,
+              out=None, stream=None):
+        """Γ, WP (float64) and kept counts (int64) as [5, n_modes] CUDA tensors."""
+        import torch
+        qs = None if q_subset is None else _np(q_subset, np.int32)
+        nm = (self.nq if qs is None else qs.size) * self.nb
+        if out is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = (torch.empty((5, nm), dtype=torch.float64, device=dev),
+                   torch.empty((5, nm), dtype=torch.float64, device=dev),
+                   torch.empty((5, nm), dtype=torch.int64, device=dev))
+        g, wp, cnt = out
+        self._check(self.lib.fc4_rates(self.ctx, float(T), 0, float(sigma_thz), int(channel_mask),
+                                       None if qs is None else _ptr(qs), 0 if qs is None else qs.size,
+                                       _tptr(g), _tptr(wp), _tptr(cnt), _stream(stream)))
+        return g, wp, cnt
+
+    def processes(self, channel: int, mode: int) -> np.ndarray:
+        n = ctypes.c_longlong(0)
+        self._check(self.lib.fc4_processes(self.ctx, channel, mode, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), np.uint64)
+        self._check(self.lib.fc4_processes(self.ctx, channel, mode, _ptr(out), n.value, ctypes.byref(n)))
+        return out[:n.value]
+
+    def kappa(self, T: float, gamma_total, out=None, stream=None):
+        import torch
+        g = gamma_total.contiguous()
+        if out is None:
+            out = torch.empty(9, dtype=torch.float64, device=g.device)
+        self._check(self.lib.fc4_kappa(self.ctx, float(T), _tptr(g), _tptr(out), _stream(stream)))
+        return out.view(3, 3)
+
+    def backward(self, dL_dgamma, dphi3=None, dphi4=None, stream=None):
+        import torch
+        dg = dL_dgamma.contiguous()
+        if dphi3 is None and self.nc3:
+            dphi3 = torch.empty((self.nc3, 27), dtype=torch.float64, device=dg.device)
+        if dphi4 is None and self.nc4:
+            dphi4 = torch.empty((self.nc4, 81), dtype=torch.float64, device=dg.device)
+        self._check(self.lib.fc4_rates_backward(self.ctx, _tptr(dg), _tptr(dphi3), _tptr(dphi4),
+                                                _stream(stream)))
+        return dphi3, dphi4
+
+    def update_anharmonic(self, phi3=None, phi4=None):
+        p3 = None if phi3 is None else _np(phi3, np.float64)
+        p4 = None if phi4 is None else _np(phi4, np.float64)
+        self._check(self.lib.fc4_update_anharmonic(self.ctx, None if p3 is None else _ptr(p3),
+                                                   None if p4 is None else _ptr(p4)))

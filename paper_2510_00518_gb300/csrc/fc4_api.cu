@@ -1,0 +1,732 @@
+// fc4_api.cu - the C interface of libfc4 (declared in include/fc4.h): argument checks, host-side
+// layout of the clusters (keys, phase indices, mass factors), device tables, and the
+// stream-ordered launch sequence of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "fc4.h"
+#include "fc4_kernels.h"
+
+namespace {
+
+// CODATA 2018 (SI)
+constexpr double kHbar = 1.054571817e-34;   // J s
+constexpr double kEv = 1.602176634e-19;     // J
+constexpr double kAmu = 1.66053906660e-27;  // kg
+constexpr double kKb = 1.380649e-23;        // J/K
+constexpr double kPi = 3.14159265358979323846;
+
+// eigenvalue of D in eV/(Å² amu) -> ω² in (rad/ps)²
+constexpr double kEigToW2 = kEv / (1e-20 * kAmu) * 1e-24;
+
+// Γ3 = C3/N Σ w|V3|², Γ4 = C4/N² Σ w|V4|² in ps^-1 for V in eV/Å^k/amu^(k/2), ω in rad/ps, δ in ps
+double unit_c3() {
+    const double fv = kEv / 1e-30 / std::pow(kAmu, 1.5);
+    return kHbar * kPi / 4.0 * fv * fv * 1e-48 * 1e-12;
+}
+double unit_c4() {
+    const double fv = kEv / 1e-40 / (kAmu * kAmu);
+    return kHbar * kHbar * kPi / 8.0 * fv * fv * 1e-60 * 1e-12;
+}
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+struct fc4_ctx {
+    fc4::Tables t{};
+    int nc2 = 0, nc3 = 0, nc4 = 0;
+    int precision = FC4_FP64, block_threads = 128;
+    bool timing = false;
+    bool allow_unstable = false;
+    cudaEvent_t ev_a[8] = {}, ev_b[8] = {};
+    bool ev_used[8] = {};
+    long long n_launches = 0;
+    double volume = 0.0;
+    std::vector<void *> owned;
+    std::vector<int> perm4;                 // device cluster slot -> input cluster index
+    std::vector<double> om_host;            // current ω (for the prefilter bound)
+    // writable views of the tables
+    double *om = nullptr, *vel = nullptr, *eig = nullptr, *invw = nullptr, *occ = nullptr;
+    double *phi3 = nullptr, *phi4 = nullptr;
+    float *om32 = nullptr, *invw32 = nullptr, *occ32 = nullptr, *phi4_32 = nullptr;
+    double2 *ev = nullptr;
+    float2 *ev32 = nullptr;
+    unsigned *vmask = nullptr;
+    int *err = nullptr;
+    double occ_T = -1.0;
+    // scratch
+    double *part_g = nullptr, *part_wp = nullptr;
+    long long *part_n = nullptr, *part_items = nullptr;
+    size_t part_cap = 0;
+    unsigned long long *stats = nullptr;    // [10] kept and items per channel of the last call
+    long long cand[5] = {0, 0, 0, 0, 0};    // candidates per channel of the last call
+    int *modes = nullptr;
+    size_t modes_cap = 0;
+    // last rates call
+    bool have_last = false;
+    double last_T = 300.0, last_sigma = 2.0 * kPi * 0.1;
+    int last_mask = 0;
+    std::vector<int> last_modes;
+    std::string last_error;
+};
+
+namespace {
+
+fc4_status fail(fc4_ctx *ctx, fc4_status s, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    else g_init_error = msg;
+    return s;
+}
+
+fc4_status cuda_fail(fc4_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? FC4_ERR_OOM : FC4_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FC4_CUDA(ctx, call)                                             \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(fc4_ctx *c, T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e == cudaSuccess) c->owned.push_back(*p);
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(fc4_ctx *c, T **p, const std::vector<T> &h) {
+    cudaError_t e = dalloc(c, p, h.size());
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
+int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
+int mod_i(long long x, int n) { long long r = x % n; return (int)(r < 0 ? r + n : r); }
+
+int4 phase_vec(const int R[3], const int mesh[3], int L) {
+    return make_int4(mod_i((long long)R[0] * (L / mesh[0]), L), mod_i((long long)R[1] * (L / mesh[1]), L),
+                     mod_i((long long)R[2] * (L / mesh[2]), L), 0);
+}
+
+fc4_status check_ifc(const fc4_ifc *f, int order, int n_atoms, bool required, const char *name) {
+    if (!f) {
+        if (required) return fail(nullptr, FC4_ERR_INVALID, std::string(name) + " is NULL");
+        return FC4_OK;
+    }
+    if (f->order != order) return fail(nullptr, FC4_ERR_INVALID, std::string(name) + ": wrong order");
+    if (f->n_clusters < 0 || (f->n_clusters > 0 && (!f->atoms || !f->cells || !f->phi)))
+        return fail(nullptr, FC4_ERR_INVALID, std::string(name) + ": bad cluster arrays");
+    if (required && f->n_clusters == 0)
+        return fail(nullptr, FC4_ERR_INVALID, std::string(name) + ": no clusters");
+    for (long long i = 0; i < (long long)f->n_clusters * order; ++i)
+        if (f->atoms[i] < 0 || f->atoms[i] >= n_atoms)
+            return fail(nullptr, FC4_ERR_INVALID, std::string(name) + ": atom index out of range");
+    for (long long i = 0; i < (long long)f->n_clusters * (order - 1) * 3; ++i)
+        if (std::abs(f->cells[i]) > 1000000)
+            return fail(nullptr, FC4_ERR_INVALID, std::string(name) + ": cell vector out of range");
+    return FC4_OK;
+}
+
+// Rebuild the derived mode tables after ω / e changed (also zeroes the excluded ω).
+fc4_status refresh_modes(fc4_ctx *c) {
+    FC4_CUDA(c, fc4::launch_mode_tables(c->t, c->om, c->om32, c->ev32, c->ev, c->vmask, c->invw,
+                                        c->invw32, 0));
+    c->om_host.assign((size_t)c->t.N * c->t.nb, 0.0);
+    FC4_CUDA(c, cudaMemcpy(c->om_host.data(), c->om, c->om_host.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    c->occ_T = -1.0;
+    return FC4_OK;
+}
+
+// Launch bracket: events on the launching stream around kernel slot k (when timing is on).
+struct Timed {
+    fc4_ctx *c;
+    int k;
+    cudaStream_t s;
+    Timed(fc4_ctx *c_, int k_, cudaStream_t s_) : c(c_), k(k_), s(s_) {
+        if (c->timing) cudaEventRecord(c->ev_a[k], s);
+    }
+    ~Timed() {
+        if (c->timing) {
+            cudaEventRecord(c->ev_b[k], s);
+            c->ev_used[k] = true;
+        }
+        c->n_launches += 1;
+    }
+};
+
+fc4_status ensure_occupations(fc4_ctx *c, double T, cudaStream_t s) {
+    if (c->occ_T == T) return FC4_OK;
+    {
+        Timed tm(c, 7, s);
+        FC4_CUDA(c, fc4::launch_occupations(c->t, kHbar * 1e12 / (kKb * T), c->occ, c->occ32, s));
+    }
+    c->occ_T = T;
+    return FC4_OK;
+}
+
+// Prefilter thresholds: |Δ32 - Δ64| <= 13 u ω_max (u = 2^-24; three roundings of the inputs'
+// partial sums plus four input roundings); margin 32 u ω_max, doubled to cover the rounding of
+// the thresholds themselves.
+void prefilter(const fc4_ctx *c, double two_sigma, float *lo, float *hi) {
+    double wmax = 0.0;
+    for (double w : c->om_host) wmax = std::max(wmax, std::fabs(w));
+    const double eps = 32.0 * std::ldexp(1.0, -24) * wmax;
+    *lo = std::nextafter((float)(two_sigma - 2.0 * eps), 0.0f);
+    *hi = std::nextafter((float)(two_sigma + 2.0 * eps), 1e30f);
+}
+
+}  // namespace
+
+extern "C" {
+
+fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_ifc *phi3,
+                    const fc4_ifc *phi4, const int mesh[3], const fc4_options *opt, fc4_ctx **out) {
+    if (!out) return fail(nullptr, FC4_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!crystal || !crystal->masses || !crystal->positions)
+        return fail(nullptr, FC4_ERR_INVALID, "crystal, masses or positions is NULL");
+    const int na = crystal->n_atoms;
+    if (na < 1 || na > fc4::kMaxAtoms)
+        return fail(nullptr, FC4_ERR_INVALID, "n_atoms must be in [1, 8]");
+    for (int i = 0; i < na; ++i)
+        if (!(crystal->masses[i] > 0.0)) return fail(nullptr, FC4_ERR_INVALID, "mass must be > 0");
+    if (!mesh || mesh[0] < 1 || mesh[1] < 1 || mesh[2] < 1 || mesh[0] > 256 || mesh[1] > 256 ||
+        mesh[2] > 256)
+        return fail(nullptr, FC4_ERR_INVALID, "mesh entries must be in [1, 256]");
+    const long long Nl = (long long)mesh[0] * mesh[1] * mesh[2];
+    if (Nl > (1 << 20)) return fail(nullptr, FC4_ERR_INVALID, "mesh has more than 2^20 points");
+    fc4_status st;
+    if ((st = check_ifc(phi2, 2, na, true, "phi2")) != FC4_OK) return st;
+    if ((st = check_ifc(phi3, 3, na, false, "phi3")) != FC4_OK) return st;
+    if ((st = check_ifc(phi4, 4, na, false, "phi4")) != FC4_OK) return st;
+    const double *A = crystal->lattice;
+    const double vol = std::fabs(A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                                 A[2] * (A[3] * A[7] - A[4] * A[6]));
+    if (!(vol > 0.0)) return fail(nullptr, FC4_ERR_INVALID, "lattice is singular");
+
+    fc4_ctx *c = new fc4_ctx();
+    if (opt) {
+        if (opt->precision != FC4_FP64 && opt->precision != FC4_MIXED) {
+            delete c;
+            return fail(nullptr, FC4_ERR_INVALID, "unknown precision");
+        }
+        c->precision = opt->precision;
+        c->timing = opt->timing != 0;
+        c->allow_unstable = opt->allow_unstable != 0;
+        if (opt->block_threads) {
+            if (opt->block_threads % 32 || opt->block_threads < 32 || opt->block_threads > 256) {
+                delete c;
+                return fail(nullptr, FC4_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 256]");
+            }
+            c->block_threads = opt->block_threads;
+        }
+    }
+    auto bail = [&](fc4_status s) {
+        g_init_error = c->last_error;
+        fc4_destroy(c);
+        return s;
+    };
+#define FC4_TRY(call)                                                               \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, #call));                \
+    } while (0)
+
+    if (c->timing)
+        for (int k = 0; k < 8; ++k) {
+            FC4_TRY(cudaEventCreate(&c->ev_a[k]));
+            FC4_TRY(cudaEventCreate(&c->ev_b[k]));
+        }
+    fc4::Tables &t = c->t;
+    const int N = (int)Nl, nb = 3 * na;
+    t.n_atoms = na;
+    t.nb = nb;
+    t.N = N;
+    for (int k = 0; k < 3; ++k) t.mesh[k] = mesh[k];
+    t.L = lcm_i(lcm_i(mesh[0], mesh[1]), mesh[2]);
+    c->volume = vol;
+    const int L = t.L;
+
+    // mesh coordinates and roots of unity
+    std::vector<int4> qc(N);
+    for (int q = 0; q < N; ++q)
+        qc[q] = make_int4(q % mesh[0], (q / mesh[0]) % mesh[1], q / (mesh[0] * mesh[1]), 0);
+    std::vector<double2> rt(L);
+    std::vector<float2> rt32(L);
+    for (int k = 0; k < L; ++k) {
+        rt[k] = make_double2(std::cos(2.0 * kPi * k / L), std::sin(2.0 * kPi * k / L));
+        rt32[k] = make_float2((float)rt[k].x, (float)rt[k].y);
+    }
+    int4 *d_qc;
+    double2 *d_rt;
+    float2 *d_rt32;
+    FC4_TRY(upload(c, &d_qc, qc));
+    FC4_TRY(upload(c, &d_rt, rt));
+    FC4_TRY(upload(c, &d_rt32, rt32));
+    t.qc = d_qc;
+    t.rt = d_rt;
+    t.rt32 = d_rt32;
+
+    auto ism = [&](std::initializer_list<int> at) {
+        double m = 1.0;
+        for (int a : at) m *= crystal->masses[a];
+        return 1.0 / std::sqrt(m);
+    };
+
+    // second order (harmonic prelude)
+    c->nc2 = phi2->n_clusters;
+    std::vector<int4> c2_at(c->nc2), c2_r(c->nc2);
+    std::vector<double> c2_R(3 * (size_t)c->nc2), c2_ism(c->nc2), c2_phi(phi2->phi, phi2->phi + 9 * (size_t)c->nc2);
+    for (int i = 0; i < c->nc2; ++i) {
+        const int a = phi2->atoms[2 * i], b = phi2->atoms[2 * i + 1];
+        const int *R = phi2->cells + 3 * i;
+        c2_at[i] = make_int4(a, b, 0, 0);
+        c2_r[i] = phase_vec(R, mesh, L);
+        for (int x = 0; x < 3; ++x) c2_R[3 * i + x] = R[0] * A[x] + R[1] * A[3 + x] + R[2] * A[6 + x];
+        c2_ism[i] = ism({a, b});
+    }
+
+    // third order
+    c->nc3 = phi3 ? phi3->n_clusters : 0;
+    t.nc3 = c->nc3;
+    {
+        std::vector<int4> at(c->nc3), r2(c->nc3), r12(c->nc3);
+        std::vector<double> im(c->nc3), ph(27 * (size_t)c->nc3);
+        for (int i = 0; i < c->nc3; ++i) {
+            const int *a = phi3->atoms + 3 * i, *R = phi3->cells + 6 * i;
+            at[i] = make_int4(a[0], a[1], a[2], 0);
+            const int d12[3] = {R[0] - R[3], R[1] - R[4], R[2] - R[5]};
+            r2[i] = phase_vec(R + 3, mesh, L);
+            r12[i] = phase_vec(d12, mesh, L);
+            im[i] = ism({a[0], a[1], a[2]});
+        }
+        if (c->nc3) std::copy(phi3->phi, phi3->phi + 27 * (size_t)c->nc3, ph.begin());
+        int4 *d_at, *d_r2, *d_r12;
+        double *d_im;
+        FC4_TRY(upload(c, &d_at, at));
+        FC4_TRY(upload(c, &d_r2, r2));
+        FC4_TRY(upload(c, &d_r12, r12));
+        FC4_TRY(upload(c, &d_im, im));
+        FC4_TRY(upload(c, &c->phi3, ph));
+        t.c3_at = d_at;
+        t.c3_r2 = d_r2;
+        t.c3_r12 = d_r12;
+        t.c3_ism = d_im;
+        t.phi3 = c->phi3;
+    }
+
+    // fourth order: key = (leg-2 atom, leg-3 atom, R2 - R3); keys ordered by group, clusters by key
+    c->nc4 = phi4 ? phi4->n_clusters : 0;
+    t.nc4 = c->nc4;
+    {
+        using Key = std::tuple<int, int, int, int>;   // group, dR
+        std::map<Key, int> key_id;
+        std::vector<Key> ck(c->nc4);
+        for (int i = 0; i < c->nc4; ++i) {
+            const int *a = phi4->atoms + 4 * i, *R = phi4->cells + 9 * i;
+            ck[i] = Key(a[2] * na + a[3], R[3] - R[6], R[4] - R[7], R[5] - R[8]);
+            key_id.emplace(ck[i], 0);
+        }
+        int nk = 0;
+        std::vector<Key> keys;
+        for (auto &kv : key_id) { kv.second = nk++; keys.push_back(kv.first); }
+        t.n_keys = nk;
+        c->perm4.resize(c->nc4);
+        std::iota(c->perm4.begin(), c->perm4.end(), 0);
+        std::stable_sort(c->perm4.begin(), c->perm4.end(),
+                         [&](int x, int y) { return key_id[ck[x]] < key_id[ck[y]]; });
+        std::vector<int> key_start(nk + 1, 0);
+        for (int i = 0; i < c->nc4; ++i) key_start[key_id[ck[i]] + 1]++;
+        for (int k = 0; k < nk; ++k) key_start[k + 1] += key_start[k];
+        for (int g = 0; g <= na * na; ++g) t.grp_start[g] = nk;
+        for (int k = nk - 1; k >= 0; --k) t.grp_start[std::get<0>(keys[k])] = k;
+        for (int g = na * na - 1; g >= 0; --g)
+            if (t.grp_start[g] > t.grp_start[g + 1]) t.grp_start[g] = t.grp_start[g + 1];
+        std::vector<int4> at(c->nc4), r3(c->nc4), r13(c->nc4), kr(nk);
+        std::vector<double> im(c->nc4), ph(81 * (size_t)c->nc4);
+        std::vector<float> im32(c->nc4), ph32(81 * (size_t)c->nc4);
+        for (int s = 0; s < c->nc4; ++s) {
+            const int i = c->perm4[s];
+            const int *a = phi4->atoms + 4 * i, *R = phi4->cells + 9 * i;
+            at[s] = make_int4(a[0], a[1], a[2], a[3]);
+            const int d13[3] = {R[0] - R[6], R[1] - R[7], R[2] - R[8]};
+            r3[s] = phase_vec(R + 6, mesh, L);
+            r13[s] = phase_vec(d13, mesh, L);
+            im[s] = ism({a[0], a[1], a[2], a[3]});
+            im32[s] = (float)im[s];
+            for (int k = 0; k < 81; ++k) {
+                ph[81 * (size_t)s + k] = phi4->phi[81 * (size_t)i + k];
+                ph32[81 * (size_t)s + k] = (float)ph[81 * (size_t)s + k];
+            }
+        }
+        for (int k = 0; k < nk; ++k) {
+            const int d[3] = {std::get<1>(keys[k]), std::get<2>(keys[k]), std::get<3>(keys[k])};
+            kr[k] = phase_vec(d, mesh, L);
+        }
+        int4 *d_at, *d_r3, *d_r13, *d_kr;
+        double *d_im;
+        float *d_im32;
+        int *d_ks;
+        FC4_TRY(upload(c, &d_at, at));
+        FC4_TRY(upload(c, &d_r3, r3));
+        FC4_TRY(upload(c, &d_r13, r13));
+        FC4_TRY(upload(c, &d_im, im));
+        FC4_TRY(upload(c, &d_im32, im32));
+        FC4_TRY(upload(c, &c->phi4, ph));
+        FC4_TRY(upload(c, &c->phi4_32, ph32));
+        FC4_TRY(upload(c, &d_ks, key_start));
+        FC4_TRY(upload(c, &d_kr, kr));
+        t.c4_at = d_at;
+        t.c4_r3 = d_r3;
+        t.c4_r13 = d_r13;
+        t.c4_ism = d_im;
+        t.c4_ism32 = d_im32;
+        t.phi4 = c->phi4;
+        t.phi4_32 = c->phi4_32;
+        t.key_start = d_ks;
+        double2 *d_P4;
+        float2 *d_P4_32;
+        FC4_TRY(dalloc(c, &d_P4, (size_t)N * nk));
+        FC4_TRY(dalloc(c, &d_P4_32, (size_t)N * nk));
+        t.P4 = d_P4;
+        t.P4_32 = d_P4_32;
+        FC4_TRY(fc4::launch_phase_tables(t, d_kr, d_P4, d_P4_32, 0));
+    }
+
+    // modes: device harmonic solve
+    const size_t nm = (size_t)N * nb;
+    FC4_TRY(dalloc(c, &c->om, nm));
+    FC4_TRY(dalloc(c, &c->vel, 3 * nm));
+    FC4_TRY(dalloc(c, &c->eig, nm));
+    FC4_TRY(dalloc(c, &c->ev, nm * nb));
+    FC4_TRY(dalloc(c, &c->ev32, nm * nb));
+    FC4_TRY(dalloc(c, &c->om32, nm));
+    FC4_TRY(dalloc(c, &c->invw, nm));
+    FC4_TRY(dalloc(c, &c->invw32, nm));
+    FC4_TRY(dalloc(c, &c->occ, nm));
+    FC4_TRY(dalloc(c, &c->occ32, nm));
+    FC4_TRY(dalloc(c, &c->vmask, (size_t)N));
+    FC4_TRY(dalloc(c, &c->err, 1));
+    FC4_TRY(cudaMemset(c->err, 0, sizeof(int)));
+    t.om = c->om;
+    t.om32 = c->om32;
+    t.vel = c->vel;
+    t.ev = c->ev;
+    t.ev32 = c->ev32;
+    t.vmask = c->vmask;
+    t.occ = c->occ;
+    t.occ32 = c->occ32;
+    t.invw = c->invw;
+    t.invw32 = c->invw32;
+    {
+        int4 *d_at, *d_r;
+        double *d_R, *d_phi, *d_ism;
+        FC4_TRY(upload(c, &d_at, c2_at));
+        FC4_TRY(upload(c, &d_r, c2_r));
+        FC4_TRY(upload(c, &d_R, c2_R));
+        FC4_TRY(upload(c, &d_phi, c2_phi));
+        FC4_TRY(upload(c, &d_ism, c2_ism));
+        FC4_TRY(fc4::launch_harmonic(t, c->nc2, d_at, d_r, d_R, d_phi, d_ism, kEigToW2, c->om, c->vel,
+                                     c->ev, c->eig, c->err, 0));
+    }
+    FC4_TRY(cudaDeviceSynchronize());
+    int herr = 0;
+    FC4_TRY(cudaMemcpy(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr && !c->allow_unstable) {
+        c->last_error = "harmonic eigenvalue below -1e-8 eV/(A^2 amu): unstable crystal";
+        return bail(FC4_ERR_UNSTABLE);
+    }
+    if (refresh_modes(c) != FC4_OK) return bail(FC4_ERR_CUDA);
+    FC4_TRY(cudaDeviceSynchronize());
+#undef FC4_TRY
+    *out = c;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_modes(fc4_ctx *c, const double *omega, const double *vel, const double *evec) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!omega || !vel || !evec) return fail(c, FC4_ERR_INVALID, "omega, vel and evec are required");
+    const size_t nm = (size_t)c->t.N * c->t.nb;
+    for (size_t i = 0; i < nm; ++i) {
+        const size_t q = i / c->t.nb, j = i % c->t.nb;
+        if (!(q == 0 && j < 3) && !(omega[i] > 0.0))
+            return fail(c, FC4_ERR_INVALID, "omega must be > 0 except for the Gamma acoustic modes");
+    }
+    FC4_CUDA(c, cudaMemcpy(c->om, omega, nm * sizeof(double), cudaMemcpyHostToDevice));
+    FC4_CUDA(c, cudaMemcpy(c->vel, vel, 3 * nm * sizeof(double), cudaMemcpyHostToDevice));
+    FC4_CUDA(c, cudaMemcpy(c->ev, evec, nm * c->t.nb * sizeof(double2), cudaMemcpyHostToDevice));
+    fc4_status s = refresh_modes(c);
+    if (s != FC4_OK) return s;
+    FC4_CUDA(c, cudaDeviceSynchronize());
+    return FC4_OK;
+}
+
+fc4_status fc4_get_modes(fc4_ctx *c, double *omega, double *vel, double *evec) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    const size_t nm = (size_t)c->t.N * c->t.nb;
+    FC4_CUDA(c, cudaDeviceSynchronize());
+    if (omega) FC4_CUDA(c, cudaMemcpy(omega, c->om, nm * sizeof(double), cudaMemcpyDeviceToHost));
+    if (vel) FC4_CUDA(c, cudaMemcpy(vel, c->vel, 3 * nm * sizeof(double), cudaMemcpyDeviceToHost));
+    if (evec) FC4_CUDA(c, cudaMemcpy(evec, c->ev, nm * c->t.nb * sizeof(double2), cudaMemcpyDeviceToHost));
+    return FC4_OK;
+}
+
+fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value,
+                     int channel_mask, const int *q_subset, int n_q, double *gamma_out,
+                     double *wp_out, long long *counts_out, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!(T_K > 0.0) || !std::isfinite(T_K)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
+    if (sigma_adaptive) return fail(c, FC4_ERR_INVALID, "adaptive broadening is not supported by fc4_rates");
+    if (!(sigma_value > 0.0) || !std::isfinite(sigma_value)) return fail(c, FC4_ERR_INVALID, "sigma must be > 0");
+    if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
+    const int N = c->t.N, nb = c->t.nb;
+    std::vector<int> modes;
+    if (q_subset) {
+        if (n_q < 0) return fail(c, FC4_ERR_INVALID, "n_q < 0");
+        modes.reserve((size_t)n_q * nb);
+        for (int i = 0; i < n_q; ++i) {
+            if (q_subset[i] < 0 || q_subset[i] >= N) return fail(c, FC4_ERR_INVALID, "q index out of range");
+            for (int j = 0; j < nb; ++j) modes.push_back(q_subset[i] * nb + j);
+        }
+    } else {
+        modes.resize((size_t)N * nb);
+        std::iota(modes.begin(), modes.end(), 0);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nm = (int)modes.size();
+    if (nm == 0) {                      // nothing to compute; outputs may be NULL
+        c->have_last = true;
+        c->last_modes.clear();
+        return FC4_OK;
+    }
+    if (!gamma_out) return fail(c, FC4_ERR_INVALID, "gamma_out is NULL");
+    if ((size_t)nm > c->modes_cap) {
+        if (c->modes) { cudaFree(c->modes); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->modes)); }
+        FC4_CUDA(c, dalloc(c, &c->modes, (size_t)nm));
+        c->modes_cap = nm;
+    }
+    const size_t need = (size_t)5 * nm * N;
+    if (need > c->part_cap) {
+        for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items})
+            if (p) { cudaFree(p); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), p)); }
+        c->part_g = c->part_wp = nullptr;
+        c->part_n = c->part_items = nullptr;
+        c->part_cap = 0;
+        FC4_CUDA(c, dalloc(c, &c->part_g, need));
+        FC4_CUDA(c, dalloc(c, &c->part_wp, need));
+        FC4_CUDA(c, dalloc(c, &c->part_n, need));
+        FC4_CUDA(c, dalloc(c, &c->part_items, need));
+        c->part_cap = need;
+    }
+    FC4_CUDA(c, cudaMemcpyAsync(c->modes, modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+    fc4_status st = ensure_occupations(c, T_K, s);
+    if (st != FC4_OK) return st;
+    const double sigma = 2.0 * kPi * sigma_value;
+    fc4::RateArgs a{};
+    a.n_modes = nm;
+    a.modes = c->modes;
+    a.two_sigma = 2.0 * sigma;
+    a.inv_sigma2 = 1.0 / (sigma * sigma);
+    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    a.part_g = c->part_g;
+    a.part_wp = c->part_wp;
+    a.part_n = c->part_n;
+    a.part_items = c->part_items;
+    if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 10));
+    FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 10 * sizeof(unsigned long long), s));
+    const int fp64 = c->precision == FC4_FP64;
+    for (int ch = 0; ch < 5; ++ch) {
+        if (!((channel_mask >> ch) & 1)) continue;
+        if (ch < 2) {
+            if (c->nc3 == 0) {
+                FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_items + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                continue;
+            }
+            Timed tm(c, ch, s);
+            FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));
+        } else {
+            if (c->nc4 == 0) {
+                FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                FC4_CUDA(c, cudaMemsetAsync(c->part_items + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                continue;
+            }
+            Timed tm(c, ch, s);
+            FC4_CUDA(c, fc4::launch_rates4(c->t, a, ch, fp64, c->block_threads, s));
+        }
+    }
+    for (int k = 0; k < 5; ++k)
+        if (!((channel_mask >> k) & 1)) c->ev_used[k] = false;
+    {
+        Timed tm(c, 5, s);
+        FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out, wp_out,
+                                       counts_out, c->stats, s));
+    }
+    for (int ch = 0; ch < 5; ++ch) {
+        const long long per = ch < 2 ? (long long)N * nb * nb : (long long)N * N * nb * nb * nb;
+        c->cand[ch] = ((channel_mask >> ch) & 1) ? per * nm : 0;
+    }
+    c->have_last = true;
+    c->last_T = T_K;
+    c->last_sigma = sigma;
+    c->last_mask = channel_mask;
+    c->last_modes = modes;
+    return FC4_OK;
+}
+
+fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *words, long long cap,
+                         long long *n_out) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (channel < 0 || channel > 4) return fail(c, FC4_ERR_INVALID, "channel must be in [0, 4]");
+    if (mode < 0 || mode >= c->t.N * c->t.nb) return fail(c, FC4_ERR_INVALID, "mode out of range");
+    if (cap < 0 || (cap > 0 && !words)) return fail(c, FC4_ERR_INVALID, "bad words / cap");
+    const long long n_thr = channel < 2 ? (long long)c->t.N * c->t.nb : (long long)c->t.N * c->t.nb * c->t.N;
+    const double two_sigma = 2.0 * c->last_sigma;
+    float lo, hi;
+    prefilter(c, two_sigma, &lo, &hi);
+    int *d_counts = nullptr;
+    long long *d_off = nullptr;
+    unsigned long long *d_words = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_counts);
+        cudaFree(d_off);
+        cudaFree(d_words);
+    };
+    cudaError_t e = cudaMalloc(&d_counts, n_thr * sizeof(int));
+    if (e == cudaSuccess) e = fc4::launch_count_processes(c->t, channel, mode, two_sigma, lo, hi, d_counts, 0);
+    std::vector<int> counts(n_thr);
+    if (e == cudaSuccess) e = cudaMemcpy(counts.data(), d_counts, n_thr * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "fc4_processes count"); }
+    std::vector<long long> off(n_thr);
+    long long total = 0;
+    for (long long i = 0; i < n_thr; ++i) { off[i] = total; total += counts[i]; }
+    if (n_out) *n_out = total;
+    if (cap > 0 && total > 0) {
+        e = cudaMalloc(&d_off, n_thr * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMalloc(&d_words, total * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemcpy(d_off, off.data(), n_thr * sizeof(long long), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = fc4::launch_write_processes(c->t, channel, mode, two_sigma, lo, hi, d_off, d_words, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(words, d_words, std::min(cap, total) * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "fc4_processes write"); }
+    }
+    cleanup();
+    return FC4_OK;
+}
+
+fc4_status fc4_kappa(fc4_ctx *c, double T_K, const double *gamma_total, double *kappa_out, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!(T_K > 0.0)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
+    if (!gamma_total || !kappa_out) return fail(c, FC4_ERR_INVALID, "NULL buffer");
+    // Σ C v v τ / (N V): v Å/ps -> m/s (1e2)², τ ps -> s (1e-12), V Å³ -> m³ (1e-30)
+    const double scale = 1e4 * 1e-12 / ((double)c->t.N * c->volume * 1e-30);
+    Timed tm(c, 6, (cudaStream_t)stream);
+    FC4_CUDA(c, fc4::launch_kappa(c->t, kHbar * 1e12 / (kKb * T_K), kKb, gamma_total, scale, kappa_out,
+                                  (cudaStream_t)stream));
+    return FC4_OK;
+}
+
+fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3, double *dphi4,
+                              void *stream) {
+    (void)dL_dgamma; (void)dphi3; (void)dphi4; (void)stream;
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!c->have_last) return fail(c, FC4_ERR_STATE, "fc4_rates_backward before fc4_rates");
+    return fail(c, FC4_ERR_STATE, "fc4_rates_backward: adjoint kernels not available in this build");
+}
+
+fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *phi4) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    FC4_CUDA(c, cudaDeviceSynchronize());
+    if (phi3 && c->nc3)
+        FC4_CUDA(c, cudaMemcpy(c->phi3, phi3, 27 * (size_t)c->nc3 * sizeof(double), cudaMemcpyHostToDevice));
+    if (phi4 && c->nc4) {
+        std::vector<double> ph(81 * (size_t)c->nc4);
+        std::vector<float> ph32(81 * (size_t)c->nc4);
+        for (int s = 0; s < c->nc4; ++s)
+            for (int k = 0; k < 81; ++k) {
+                ph[81 * (size_t)s + k] = phi4[81 * (size_t)c->perm4[s] + k];
+                ph32[81 * (size_t)s + k] = (float)ph[81 * (size_t)s + k];
+            }
+        FC4_CUDA(c, cudaMemcpy(c->phi4, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice));
+        FC4_CUDA(c, cudaMemcpy(c->phi4_32, ph32.data(), ph32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return FC4_OK;
+}
+
+fc4_status fc4_stats(fc4_ctx *c, long long out[15]) {
+    if (!c || !out) return fail(c, FC4_ERR_INVALID, "NULL argument");
+    if (!c->have_last || !c->stats) return fail(c, FC4_ERR_STATE, "fc4_stats before fc4_rates");
+    unsigned long long h[10];
+    FC4_CUDA(c, cudaDeviceSynchronize());
+    FC4_CUDA(c, cudaMemcpy(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int ch = 0; ch < 5; ++ch) {
+        out[3 * ch] = (long long)h[2 * ch];
+        out[3 * ch + 1] = (long long)h[2 * ch + 1];
+        out[3 * ch + 2] = c->cand[ch];
+    }
+    return FC4_OK;
+}
+
+fc4_status fc4_timings(fc4_ctx *c, double out[9]) {
+    if (!c || !out) return fail(c, FC4_ERR_INVALID, "NULL argument");
+    if (!c->timing) return fail(c, FC4_ERR_STATE, "timing was not enabled in fc4_options");
+    for (int k = 0; k < 8; ++k) {
+        out[k] = 0.0;
+        if (!c->ev_used[k]) continue;
+        FC4_CUDA(c, cudaEventSynchronize(c->ev_b[k]));
+        float ms = 0.0f;
+        FC4_CUDA(c, cudaEventElapsedTime(&ms, c->ev_a[k], c->ev_b[k]));
+        out[k] = ms;
+    }
+    out[8] = (double)c->n_launches;
+    return FC4_OK;
+}
+
+fc4_status fc4_info(const fc4_ctx *c, long long out[8]) {
+    if (!c || !out) return FC4_ERR_INVALID;
+    out[0] = c->t.n_atoms;
+    out[1] = c->t.nb;
+    out[2] = c->t.N;
+    out[3] = c->nc2;
+    out[4] = c->nc3;
+    out[5] = c->nc4;
+    out[6] = c->t.n_keys;
+    out[7] = c->precision;
+    return FC4_OK;
+}
+
+const char *fc4_last_error(const fc4_ctx *c) {
+    return c ? c->last_error.c_str() : g_init_error.c_str();
+}
+
+void fc4_destroy(fc4_ctx *c) {
+    if (!c) return;
+    for (int k = 0; k < 8; ++k) {
+        if (c->ev_a[k]) cudaEventDestroy(c->ev_a[k]);
+        if (c->ev_b[k]) cudaEventDestroy(c->ev_b[k]);
+    }
+    for (void *p : c->owned) cudaFree(p);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// fc4_kernels.h - launch interfaces of libfc4's kernels (host side), shared between the C-ABI
+// translation unit and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fc4 {
+
+constexpr int kMaxAtoms = 8;      // nb <= 24: branch masks fit in 32 bits
+constexpr int kGroups = kMaxAtoms * kMaxAtoms + 1;   // (leg-2 atom, leg-3 atom) groups + 1
+
+// Device tables of one context (all pointers are device memory).
+struct Tables {
+    int n_atoms, nb, N, L;
+    int mesh[3];
+    // mesh
+    const int4 *qc;              // [N] integer coordinates (i1, i2, i3, 0)
+    const double2 *rt;           // [L] exp(2πi k / L)
+    const float2 *rt32;          // [L]
+    // modes
+    const double *om;            // [N*nb] rad/ps (0 for excluded)
+    const float *om32;           // [N*nb]
+    const double *vel;           // [N*nb][3] Å/ps
+    const double2 *ev;           // [N][nb comp][nb branch]
+    const float2 *ev32;          // [N][nb][nb]
+    const unsigned *vmask;       // [N] bit j set iff mode (q, j) takes part
+    // occupations at the current T
+    const double *occ;           // [N*nb]
+    const float *occ32;          // [N*nb]
+    const double *invw;          // [N*nb] 1/ω (0 for excluded)
+    const float *invw32;         // [N*nb]
+    // third order
+    int nc3;
+    const int4 *c3_at;           // [nc3] (a, b, c, 0)
+    const int4 *c3_r2;           // [nc3] R2 (L/n) mod L
+    const int4 *c3_r12;          // [nc3] (R1 - R2)(L/n) mod L
+    const double *c3_ism;        // [nc3] 1/sqrt(m_a m_b m_c)
+    const double *phi3;          // [nc3][27]
+    // fourth order: clusters sorted by key; keys sorted by (leg-2 atom, leg-3 atom) group
+    int nc4, n_keys;
+    const int4 *c4_at;           // [nc4] (a, b, c, d)
+    const int4 *c4_r3;           // [nc4] R3 (L/n) mod L
+    const int4 *c4_r13;          // [nc4] (R1 - R3)(L/n) mod L
+    const double *c4_ism;        // [nc4] 1/sqrt(m_a m_b m_c m_d)
+    const float *c4_ism32;
+    const double *phi4;          // [nc4][81]
+    const float *phi4_32;
+    const int *key_start;        // [n_keys + 1] cluster range of each key
+    const double2 *P4;           // [N][n_keys] exp(i q.(R2 - R3)) of each key
+    const float2 *P4_32;
+    int grp_start[kGroups];      // key range of group g = c * n_atoms + d
+};
+
+// Per-call parameters of the rate kernels.
+struct RateArgs {
+    int n_modes;                 // modes in the subset (n_q * nb)
+    const int *modes;            // [n_modes] device
+    double two_sigma;            // 2σ (rad/ps)
+    double inv_sigma2;           // 1/σ²
+    double gnorm;                // 1/(σ sqrt(π))
+    float lo32, hi32;            // prefilter: |Δ32| <= lo keep, > hi reject, else exact
+    double *part_g;              // [5][n_modes][N] per-(mode, q') partial sums
+    double *part_wp;
+    long long *part_n;           // kept processes
+    long long *part_items;       // 4ph: (q'', j''') items evaluated; 3ph: 0
+};
+
+// launchers (stream-ordered; return cudaGetLastError())
+cudaError_t launch_rates3(const Tables &t, const RateArgs &a, int ch, int fp64, cudaStream_t s);
+cudaError_t launch_rates4(const Tables &t, const RateArgs &a, int ch, int fp64, int threads,
+                          cudaStream_t s);
+cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3,
+                          double c4, double *gamma, double *wp, long long *counts,
+                          unsigned long long *stats, cudaStream_t s);
+cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const int4 *c2_r,
+                            const double *c2_R, const double *c2_phi, const double *c2_ism,
+                            double eig_to_w2, double *om, double *vel, double2 *ev, double *eig,
+                            int *err, cudaStream_t s);
+cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float2 *ev32,
+                               const double2 *ev, unsigned *vmask, double *invw, float *invw32,
+                               cudaStream_t s);
+cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ, float *occ32,
+                               cudaStream_t s);
+cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4, float2 *P4_32,
+                                cudaStream_t s);
+cudaError_t launch_kappa(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
+                         double scale, double *kappa, cudaStream_t s);
+cudaError_t launch_count_processes(const Tables &t, int ch, int mode, double two_sigma,
+                                   float lo32, float hi32, int *counts, cudaStream_t s);
+cudaError_t launch_write_processes(const Tables &t, int ch, int mode, double two_sigma,
+                                   float lo32, float hi32, const long long *offsets,
+                                   unsigned long long *words, cudaStream_t s);
+
+}  // namespace fc4

@@ -1,0 +1,286 @@
+// k_rates4.cuh - fused four-phonon kernel: enumeration, energy window, matrix element V4,
+// weight and per-(λ, q') reduction, for one channel (++, +-, --).
+//
+// The paper (Algorithms 3-4) enumerates the kept processes on the CPU, ships index lists to
+// the GPU and evaluates V per process.  Here the same work is fused and factored so that the
+// dense parts are shared.  One thread block owns a unit (λ = (q, j), q') and loops over the
+// partner branch j'.  With q''' = q + s1 q' + s2 q'', the phase of a cluster factorises as
+//   exp(i(s1 q'.R1 + s2 q''.R2 - q'''.R3)) = exp(-i q.R3) exp(i s1 q'.(R1 - R3)) exp(i s2 q''.(R2 - R3)),
+// so with a "key" r = (leg-2 atom c, leg-3 atom d, R2 - R3) the element is
+//   V = Σ_r P_r(q'')^s2 Σ_γδ W_r[γδ] e^s2_λ''(cγ) e*_λ'''(dδ),
+//   W_r[γδ] = Σ_{clusters in r} exp(-i q.R3 + i s1 q'.(R1 - R3)) / sqrt(m) Σ_αβ Φ[αβγδ] e_λ(aα) e^s1_λ'(bβ),
+// W built once per (λ, q', j') in shared memory.  Partners q'' are enumerated one per thread,
+// the window is tested with an FP32 prefilter of proven error bound (ambiguous cases are
+// decided by the exact FP64 Δ), kept (q'', j''', j''-mask) items are compacted in order by a
+// block scan, and each item computes Y[cγ] = Σ_r P_r Σ_δ W_r[γδ] e*_λ'''(dδ) once for all its
+// j'' (V = Σ_cγ e^s2_λ''(cγ) Y[cγ]).
+#pragma once
+#include "fc4_device.cuh"
+#include "fc4_kernels.h"
+
+namespace fc4 {
+
+template <typename R>
+struct Sel {
+    static __device__ __forceinline__ const Cplx<R> *ev(const Tables &t);
+    static __device__ __forceinline__ const Cplx<R> *rt(const Tables &t);
+    static __device__ __forceinline__ const Cplx<R> *P4(const Tables &t);
+    static __device__ __forceinline__ const R *phi4(const Tables &t);
+    static __device__ __forceinline__ const R *ism4(const Tables &t);
+    static __device__ __forceinline__ const R *occ(const Tables &t);
+    static __device__ __forceinline__ const R *invw(const Tables &t);
+};
+template <> struct Sel<double> {
+    static __device__ __forceinline__ const double2 *ev(const Tables &t) { return t.ev; }
+    static __device__ __forceinline__ const double2 *rt(const Tables &t) { return t.rt; }
+    static __device__ __forceinline__ const double2 *P4(const Tables &t) { return t.P4; }
+    static __device__ __forceinline__ const double *phi4(const Tables &t) { return t.phi4; }
+    static __device__ __forceinline__ const double *ism4(const Tables &t) { return t.c4_ism; }
+    static __device__ __forceinline__ const double *occ(const Tables &t) { return t.occ; }
+    static __device__ __forceinline__ const double *invw(const Tables &t) { return t.invw; }
+};
+template <> struct Sel<float> {
+    static __device__ __forceinline__ const float2 *ev(const Tables &t) { return t.ev32; }
+    static __device__ __forceinline__ const float2 *rt(const Tables &t) { return t.rt32; }
+    static __device__ __forceinline__ const float2 *P4(const Tables &t) { return t.P4_32; }
+    static __device__ __forceinline__ const float *phi4(const Tables &t) { return t.phi4_32; }
+    static __device__ __forceinline__ const float *ism4(const Tables &t) { return t.c4_ism32; }
+    static __device__ __forceinline__ const float *occ(const Tables &t) { return t.occ32; }
+    static __device__ __forceinline__ const float *invw(const Tables &t) { return t.invw32; }
+};
+
+// Exact FP64 decision for the rare candidates inside the prefilter's ambiguity band (kept out of
+// line: the unrolled branch loops stay small).
+static __device__ __noinline__ bool window_exact4(int ch, double w0, double w1, double w2, double w3,
+                                            double two_sigma) {
+    return fabs(delta_exact(ch, w0, w1, w2, w3)) <= two_sigma;
+}
+
+// symmetry factor of the 4ph channels: 1/2 (++, +-), 1/6 (--)
+template <typename R> __device__ __forceinline__ R sym4(int ch) { return ch == 4 ? R(1) / R(6) : R(0.5); }
+
+template <typename R, int NA>
+__global__ void __launch_bounds__(256)
+rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    const int s1 = (ch == 4) ? -1 : 1;
+    const int s2 = (ch == 2) ? 1 : -1;
+    const int N = t.N;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *sW = reinterpret_cast<C *>(smem);                        // [n_keys * 9]
+    C *sE = sW + t.n_keys * 9;                                  // [NA*NA*9]  e_λ(aα) e^s1_λ'(bβ)
+    C *se0 = sE + NA * NA * 9;                                  // [NB]       e_λ
+    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(se0 + NB + (NB & 1));  // [blockDim * NB]
+    __shared__ int s_scan[32];
+    __shared__ double s_red[32];
+    __shared__ long long s_redn[32];
+
+    const int unit = blockIdx.x;
+    const int ms = unit / N, q1 = unit - ms * N;
+    const int m0 = a.modes[ms];
+    const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+    const C *ev = Sel<R>::ev(t);
+    const C *rt = Sel<R>::rt(t);
+    const C *P4 = Sel<R>::P4(t);
+    const R *phi4 = Sel<R>::phi4(t);
+    const R *ism4 = Sel<R>::ism4(t);
+    const R *occ = Sel<R>::occ(t);
+    const R *invw = Sel<R>::invw(t);
+
+    double acc_g = 0.0, acc_wp = 0.0;
+    long long acc_n = 0, acc_items = 0;
+
+    const bool active = !(q0 == 0 && j0 < 3);
+    if (active) {
+        const int4 c0 = t.qc[q0], c1 = t.qc[q1];
+        const int b0 = c0.x + s1 * c1.x, b1 = c0.y + s1 * c1.y, b2 = c0.z + s1 * c1.z;
+        const double w0 = t.om[m0];
+        const float w0f = t.om32[m0];
+        const unsigned vm1 = t.vmask[q1];
+        for (int k = threadIdx.x; k < NB; k += blockDim.x) se0[k] = ev[(q0 * NB + k) * NB + j0];
+
+        for (int j1 = 0; j1 < NB; ++j1) {
+            if (!((vm1 >> j1) & 1u)) continue;
+            const int m1 = q1 * NB + j1;
+            __syncthreads();                       // previous j1 finished with sW / sE / sQ
+            for (int k = threadIdx.x; k < NA * NA * 9; k += blockDim.x) {
+                const int ab = k / 9, ij = k - ab * 9;
+                const int at = ab / NA, bt = ab - at * NA;
+                const int al = ij / 3, be = ij - al * 3;
+                C y = cconj_if(ev[(q1 * NB + 3 * bt + be) * NB + j1], s1 < 0);
+                sE[k] = cmul(se0[3 * at + al], y);
+            }
+            __syncthreads();
+            // W_r[γδ], one entry per thread; clusters of a key summed in order (deterministic)
+            for (int k = threadIdx.x; k < t.n_keys * 9; k += blockDim.x) {
+                const int r = k / 9, gd = k - r * 9;
+                C acc = czero<C>();
+                for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c) {
+                    const int4 at = t.c4_at[c];
+                    const int idx = mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) -
+                                                phase_index(c0, t.c4_r3[c], t.L), t.L);
+                    const R *ph4 = phi4 + 81 * c + gd;
+                    const C *E = sE + (at.x * NA + at.y) * 9;
+                    C s = czero<C>();
+#pragma unroll
+                    for (int ab = 0; ab < 9; ++ab) s = crfma(ph4[9 * ab], E[ab], s);
+                    acc = crfma(ism4[c], cmul(rt[idx], s), acc);
+                }
+                sW[k] = acc;
+            }
+            __syncthreads();
+
+            const float base32 = w0f + (float)s1 * t.om32[m1];
+            const double w1 = t.om[m1];
+            for (int q2base = 0; q2base < N; q2base += blockDim.x) {
+                const int q2 = q2base + threadIdx.x;
+                unsigned mask[NB];
+                int n_items = 0;
+                if (q2 < N) {
+                    const int4 c2 = t.qc[q2];
+                    const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                           t.mesh[0], t.mesh[1], t.mesh[2]);
+                    const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+                    float t2[NB], w3f[NB];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        t2[j] = base32 + (float)s2 * t.om32[q2 * NB + j];
+                        w3f[j] = t.om32[q3 * NB + j];
+                    }
+#pragma unroll
+                    for (int j3 = 0; j3 < NB; ++j3) {
+                        unsigned m = 0;
+                        if ((v3 >> j3) & 1u) {
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2) {
+                                if (!((v2 >> j2) & 1u)) continue;
+                                const float ad = fabsf(t2[j2] - w3f[j3]);
+                                bool keep;
+                                if (ad <= a.lo32) keep = true;
+                                else if (ad > a.hi32) keep = false;
+                                else keep = window_exact4(ch, w0, w1, t.om[q2 * NB + j2],
+                                                          t.om[q3 * NB + j3], a.two_sigma);
+                                m |= (unsigned)keep << j2;
+                            }
+                        }
+                        mask[j3] = m;
+                        n_items += (m != 0);
+                    }
+                } else {
+#pragma unroll
+                    for (int j3 = 0; j3 < NB; ++j3) mask[j3] = 0;
+                }
+                int total;
+                int off = block_exclusive_scan(n_items, s_scan, &total);
+#pragma unroll
+                for (int j3 = 0; j3 < NB; ++j3)
+                    if (mask[j3])
+                        sQ[off++] = ((unsigned long long)q2 << 32) | ((unsigned long long)j3 << 24) | mask[j3];
+                __syncthreads();
+
+                for (int it = threadIdx.x; it < total; it += blockDim.x) {
+                    ++acc_items;
+                    const unsigned long long item = sQ[it];
+                    const int iq2 = (int)(item >> 32);
+                    const int j3 = (int)((item >> 24) & 0xff);
+                    unsigned m = (unsigned)(item & 0xffffffu);
+                    const int4 c2 = t.qc[iq2];
+                    const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                           t.mesh[0], t.mesh[1], t.mesh[2]);
+                    // Y[cγ] = Σ_d Σ_{r in (c,d)} P_r^s2 Σ_δ W_r[γδ] e*_λ'''(dδ)
+                    C Y[NA][3];
+#pragma unroll
+                    for (int c = 0; c < NA; ++c)
+#pragma unroll
+                        for (int g = 0; g < 3; ++g) Y[c][g] = czero<C>();
+                    const C *P = P4 + (size_t)iq2 * t.n_keys;
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) {
+#pragma unroll
+                        for (int d = 0; d < NA; ++d) {
+                            const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
+                            if (r0 == r1) continue;
+                            C e3[3];
+#pragma unroll
+                            for (int dl = 0; dl < 3; ++dl)
+                                e3[dl] = cconj(ev[(q3 * NB + 3 * d + dl) * NB + j3]);
+                            for (int r = r0; r < r1; ++r) {
+                                const C ph = cconj_if(P[r], s2 < 0);
+                                const C *Wr = sW + 9 * r;
+#pragma unroll
+                                for (int g = 0; g < 3; ++g) {
+                                    C u = cmul(Wr[3 * g], e3[0]);
+                                    u = cfma(Wr[3 * g + 1], e3[1], u);
+                                    u = cfma(Wr[3 * g + 2], e3[2], u);
+                                    Y[c][g] = cfma(ph, u, Y[c][g]);
+                                }
+                            }
+                        }
+                    }
+                    const int m3 = q3 * NB + j3;
+                    const double w3 = t.om[m3];
+                    const R n3 = occ[m3], iw3 = invw[m3];
+                    while (m) {
+                        const int j2 = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int m2 = iq2 * NB + j2;
+                        C V = czero<C>();
+#pragma unroll
+                        for (int c = 0; c < NA; ++c)
+#pragma unroll
+                            for (int g = 0; g < 3; ++g)
+                                V = cfma(cconj_if(ev[(iq2 * NB + 3 * c + g) * NB + j2], s2 < 0), Y[c][g], V);
+                        const double d = delta_exact(ch, w0, w1, t.om[m2], w3);
+                        R w;
+                        if constexpr (sizeof(R) == 8) {
+                            const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                            w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
+                                g * invw[m0] * invw[m1] * invw[m2] * iw3;
+                        } else {
+                            const float df = (float)d;
+                            const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
+                            w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
+                                (invw[m0] * invw[m1]) * (invw[m2] * iw3);
+                        }
+                        acc_wp += (double)w;
+                        acc_g += (double)w * cabs2(V);
+                        acc_n += 1;
+                    }
+                }
+                __syncthreads();                   // sQ reused by the next chunk
+            }
+        }
+    }
+    const double g = block_sum(acc_g, s_red);
+    const double wp = block_sum(acc_wp, s_red);
+    const long long n = block_sum(acc_n, s_redn);
+    const long long ni = block_sum(acc_items, s_redn);
+    if (threadIdx.x == 0) {
+        const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
+        a.part_g[o] = g;
+        a.part_wp[o] = wp;
+        a.part_n[o] = n;
+        a.part_items[o] = ni;
+    }
+}
+
+template <typename R, int NA>
+cudaError_t launch4(const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    size_t smem = sizeof(C) * ((size_t)t.n_keys * 9 + NA * NA * 9 + NB + (NB & 1)) +
+                  sizeof(unsigned long long) * (size_t)threads * NB;
+    smem = (smem + 15) & ~size_t(15);
+    cudaError_t e = cudaFuncSetAttribute(rates4_kernel<R, NA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long units = (long long)a.n_modes * t.N;
+    if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (units == 0) return cudaSuccess;
+    rates4_kernel<R, NA><<<(unsigned)units, threads, smem, s>>>(t, a, ch);
+    return cudaGetLastError();
+}
+
+}  // namespace fc4

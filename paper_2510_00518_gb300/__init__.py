@@ -75,6 +75,7 @@ def load(build_if_missing: bool = False):
         "fc4_info": [vp, vp],
         "fc4_stats": [vp, vp],
         "fc4_timings": [vp, vp],
+        "fc4_rates_static": [vp, d, d, i, vp, i, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -232,6 +233,23 @@ class Engine:
         self._check(self.lib.fc4_rates(self.ctx, float(T), 0, float(sigma_thz), int(channel_mask),
                                        None if qs is None else _ptr(qs), 0 if qs is None else qs.size,
                                        _tptr(g), _tptr(wp), _tptr(cnt), _stream(stream)))
+        return g, wp, cnt
+
+    def rates_static(self, T: float, sigma_thz: float, channel_mask: int, q_subset, out=None, stream=None):
+        """fc4_rates_static: rates without any device allocation inside the call (the scratch is
+        the library's fixed device array; n_q * nb * N <= 65536).  Outputs as in ``rates``."""
+        import torch
+        qs = _np(q_subset, np.int32)
+        nm = qs.size * self.nb
+        if out is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = (torch.empty((5, nm), dtype=torch.float64, device=dev),
+                   torch.empty((5, nm), dtype=torch.float64, device=dev),
+                   torch.empty((5, nm), dtype=torch.int64, device=dev))
+        g, wp, cnt = out
+        self._check(self.lib.fc4_rates_static(self.ctx, float(T), float(sigma_thz), int(channel_mask),
+                                              _ptr(qs), qs.size, _tptr(g), _tptr(wp), _tptr(cnt),
+                                              _stream(stream)))
         return g, wp, cnt
 
     def processes(self, channel: int, mode: int) -> np.ndarray:

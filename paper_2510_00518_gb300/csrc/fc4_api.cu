@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -730,3 +731,112 @@ void fc4_destroy(fc4_ctx *c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ allocation-free rates
+//
+// fc4_rates_static: the same kernels as fc4_rates, but every piece of per-call device scratch (the
+// q list, the mode list and the per-(channel, mode, q') partial sums) lives in one file-scope
+// __device__ array of fixed size, so the call itself allocates no device memory.  A host-side use
+// of the array's name is only a stand-in for it; the device address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+
+namespace {
+
+constexpr long long kStaticUnits = 1LL << 16;       // max (modes x q') units per channel
+constexpr long long kStaticQ = kStaticUnits;         // max q points (n_q <= units)
+constexpr size_t kStaticBytes =
+    5 * (size_t)kStaticUnits * (2 * sizeof(double) + 2 * sizeof(long long)) +
+    2 * (size_t)kStaticQ * sizeof(int);
+
+static __device__ __align__(256) unsigned char g_fc4_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 256;
+unsigned char *g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mu;
+
+// Device address of the scratch array on the current device (looked up on first use).
+cudaError_t static_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fc4_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void expand_modes_kernel(const int *qs, int n_q, int nb, int *modes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_q * nb) modes[i] = qs[i / nb] * nb + (i % nb);
+}
+
+}  // namespace
+
+extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_value, int channel_mask,
+                                       const int *q_subset, int n_q, double *gamma_out,
+                                       double *wp_out, long long *counts_out, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!(T_K > 0.0) || !std::isfinite(T_K)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
+    if (!(sigma_value > 0.0) || !std::isfinite(sigma_value)) return fail(c, FC4_ERR_INVALID, "sigma must be > 0");
+    if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
+    if (!q_subset || n_q < 0) return fail(c, FC4_ERR_INVALID, "q_subset is required");
+    const int N = c->t.N, nb = c->t.nb;
+    for (int i = 0; i < n_q; ++i)
+        if (q_subset[i] < 0 || q_subset[i] >= N) return fail(c, FC4_ERR_INVALID, "q index out of range");
+    const long long nm = (long long)n_q * nb;
+    if (nm * N > kStaticUnits)
+        return fail(c, FC4_ERR_INVALID, "fc4_rates_static: n_q * nb * N exceeds 65536 (static scratch limit)");
+    if (nm == 0) return FC4_OK;
+    if (!gamma_out) return fail(c, FC4_ERR_INVALID, "gamma_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *base = nullptr;
+    FC4_CUDA(c, static_scratch(&base));
+    const size_t units = (size_t)kStaticUnits;
+    double *part_g = reinterpret_cast<double *>(base);
+    double *part_wp = part_g + 5 * units;
+    long long *part_n = reinterpret_cast<long long *>(part_wp + 5 * units);
+    long long *part_items = part_n + 5 * units;
+    int *d_q = reinterpret_cast<int *>(part_items + 5 * units);
+    int *d_modes = d_q + kStaticQ;
+    FC4_CUDA(c, cudaMemcpyAsync(d_q, q_subset, (size_t)n_q * sizeof(int), cudaMemcpyHostToDevice, s));
+    expand_modes_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(d_q, n_q, nb, d_modes);
+    FC4_CUDA(c, cudaGetLastError());
+    fc4_status st = ensure_occupations(c, T_K, s);
+    if (st != FC4_OK) return st;
+    const double sigma = 2.0 * kPi * sigma_value;
+    fc4::RateArgs a{};
+    a.n_modes = (int)nm;
+    a.modes = d_modes;
+    a.two_sigma = 2.0 * sigma;
+    a.inv_sigma2 = 1.0 / (sigma * sigma);
+    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    a.part_g = part_g;
+    a.part_wp = part_wp;
+    a.part_n = part_n;
+    a.part_items = part_items;
+    const int fp64 = c->precision == FC4_FP64;
+    const size_t chunk = (size_t)nm * N;
+    for (int ch = 0; ch < 5; ++ch) {
+        if (!((channel_mask >> ch) & 1)) continue;
+        const bool empty = ch < 2 ? c->nc3 == 0 : c->nc4 == 0;
+        if (empty) {                                   // the only partials read without a write
+            FC4_CUDA(c, cudaMemsetAsync(part_g + ch * chunk, 0, chunk * sizeof(double), s));
+            FC4_CUDA(c, cudaMemsetAsync(part_wp + ch * chunk, 0, chunk * sizeof(double), s));
+            FC4_CUDA(c, cudaMemsetAsync(part_n + ch * chunk, 0, chunk * sizeof(long long), s));
+            FC4_CUDA(c, cudaMemsetAsync(part_items + ch * chunk, 0, chunk * sizeof(long long), s));
+            continue;
+        }
+        if (ch < 2) FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));
+        else FC4_CUDA(c, fc4::launch_rates4(c->t, a, ch, fp64, c->block_threads, s));
+    }
+    FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out, wp_out,
+                                   counts_out, nullptr, s));
+    return FC4_OK;
+}

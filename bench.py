@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--cpu-qp", type=int, default=24, help="oracle sample: partners q' < cpu_qp")
     p.add_argument("--cpu-q", type=int, default=2, help="oracle sample: q points (x nb modes)")
     p.add_argument("--block-threads", type=int, default=0)
+    p.add_argument("--once", action="store_true",
+                   help="one untimed fc4_rates call (for profilers): --mesh, --precision, --mask")
+    p.add_argument("--mask", type=int, default=31, help="channel mask of --once")
     return p.parse_args()
 
 
@@ -325,9 +328,23 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_once(args):
+    """A single rates call on the workload (profiling helper, no timing, no JSON line)."""
+    import torch
+    from paper_2510_00518_gb300 import Engine, FP64, MIXED
+    sysm, mesh = workload(args, seed=0)
+    eng = Engine(*sysm, mesh, precision=MIXED if args.precision == "mixed" else FP64,
+                 block_threads=args.block_threads)
+    g, _, _ = eng.rates(args.T, args.sigma, args.mask)
+    torch.cuda.synchronize()
+    print("once", args.mesh, args.precision, args.mask, float(g.sum()), eng.stats())
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.once:
+        run_once(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)

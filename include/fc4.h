@@ -74,7 +74,7 @@ typedef struct {
 
 typedef struct {
     int precision;            /* fc4_precision */
-    int block_threads;        /* threads per block of the 4ph kernel; 0 = default (128) */
+    int block_threads;        /* threads per block of the 4ph kernel: 64, 96 or 128; 0 = 128 */
     long long timeout_cycles; /* bound of device-side waits; 0 = default */
     int timing;               /* 1: record CUDA events around every kernel launch (fc4_timings) */
     int allow_unstable;       /* 1: fc4_init keeps a crystal with imaginary modes (ω set to 0 for them) */

@@ -56,7 +56,7 @@ struct fc4_ctx {
     // writable views of the tables
     double *om = nullptr, *vel = nullptr, *eig = nullptr, *invw = nullptr, *occ = nullptr;
     double *phi3 = nullptr, *phi4 = nullptr;
-    float *om32 = nullptr, *invw32 = nullptr, *occ32 = nullptr, *phi4_32 = nullptr;
+    float *om32 = nullptr, *om32lo = nullptr, *invw32 = nullptr, *occ32 = nullptr, *phi4_32 = nullptr;
     double2 *ev = nullptr;
     float2 *ev32 = nullptr;
     unsigned *vmask = nullptr;
@@ -70,6 +70,8 @@ struct fc4_ctx {
     long long cand[5] = {0, 0, 0, 0, 0};    // candidates per channel of the last call
     int *modes = nullptr;
     size_t modes_cap = 0;
+    void *wbuf = nullptr;                  // W scratch of the tiled 4ph path
+    size_t wbuf_bytes = 0;
     // last rates call
     bool have_last = false;
     double last_T = 300.0, last_sigma = 2.0 * kPi * 0.1;
@@ -144,8 +146,8 @@ fc4_status check_ifc(const fc4_ifc *f, int order, int n_atoms, bool required, co
 
 // Rebuild the derived mode tables after ω / e changed (also zeroes the excluded ω).
 fc4_status refresh_modes(fc4_ctx *c) {
-    FC4_CUDA(c, fc4::launch_mode_tables(c->t, c->om, c->om32, c->ev32, c->ev, c->vmask, c->invw,
-                                        c->invw32, 0));
+    FC4_CUDA(c, fc4::launch_mode_tables(c->t, c->om, c->om32, c->om32lo, c->ev32, c->ev, c->vmask,
+                                        c->invw, c->invw32, 0));
     c->om_host.assign((size_t)c->t.N * c->t.nb, 0.0);
     FC4_CUDA(c, cudaMemcpy(c->om_host.data(), c->om, c->om_host.size() * sizeof(double),
                            cudaMemcpyDeviceToHost));
@@ -230,9 +232,9 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
         c->timing = opt->timing != 0;
         c->allow_unstable = opt->allow_unstable != 0;
         if (opt->block_threads) {
-            if (opt->block_threads % 32 || opt->block_threads < 32 || opt->block_threads > 256) {
+            if (opt->block_threads % 32 || opt->block_threads < 64 || opt->block_threads > 128) {
                 delete c;
-                return fail(nullptr, FC4_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 256]");
+                return fail(nullptr, FC4_ERR_INVALID, "block_threads must be 64, 96 or 128");
             }
             c->block_threads = opt->block_threads;
         }
@@ -417,6 +419,7 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     FC4_TRY(dalloc(c, &c->ev, nm * nb));
     FC4_TRY(dalloc(c, &c->ev32, nm * nb));
     FC4_TRY(dalloc(c, &c->om32, nm));
+    FC4_TRY(dalloc(c, &c->om32lo, nm));
     FC4_TRY(dalloc(c, &c->invw, nm));
     FC4_TRY(dalloc(c, &c->invw32, nm));
     FC4_TRY(dalloc(c, &c->occ, nm));
@@ -426,6 +429,7 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     FC4_TRY(cudaMemset(c->err, 0, sizeof(int)));
     t.om = c->om;
     t.om32 = c->om32;
+    t.om32lo = c->om32lo;
     t.vel = c->vel;
     t.ev = c->ev;
     t.ev32 = c->ev32;
@@ -549,6 +553,27 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     a.part_wp = c->part_wp;
     a.part_n = c->part_n;
     a.part_items = c->part_items;
+    {   // W scratch of the tiled 4ph path: up to 4 GiB, in whole modes, grown on demand
+        const size_t per_mode = fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64);
+        if (per_mode && (channel_mask & 0b11100) && c->nc4) {
+            const size_t cap_modes = std::max<size_t>(1, std::min<size_t>((size_t)nm, (4ull << 30) / per_mode));
+            const size_t want = cap_modes * per_mode;
+            if (c->wbuf_bytes < want) {
+                if (c->wbuf) {
+                    cudaFree(c->wbuf);
+                    c->owned.erase(std::find(c->owned.begin(), c->owned.end(), c->wbuf));
+                    c->wbuf = nullptr;
+                    c->wbuf_bytes = 0;
+                }
+                unsigned char *w = nullptr;
+                FC4_CUDA(c, dalloc(c, &w, want));
+                c->wbuf = w;
+                c->wbuf_bytes = want;
+            }
+        }
+        a.wbuf = c->wbuf;
+        a.wbuf_bytes = c->wbuf_bytes;
+    }
     if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 10));
     FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 10 * sizeof(unsigned long long), s));
     const int fp64 = c->precision == FC4_FP64;

@@ -20,7 +20,8 @@ struct Tables {
     const float2 *rt32;          // [L]
     // modes
     const double *om;            // [N*nb] rad/ps (0 for excluded)
-    const float *om32;           // [N*nb]
+    const float *om32;           // [N*nb] ω rounded to FP32 (hi part)
+    const float *om32lo;         // [N*nb] ω - hi rounded to FP32 (lo part)
     const double *vel;           // [N*nb][3] Å/ps
     const double2 *ev;           // [N][nb comp][nb branch]
     const float2 *ev32;          // [N][nb][nb]
@@ -64,12 +65,18 @@ struct RateArgs {
     double *part_wp;
     long long *part_n;           // kept processes
     long long *part_items;       // 4ph: (q'', j''') items evaluated; 3ph: 0
+    int n_part[5];               // partial slots written per mode for each channel (<= N)
+    void *wbuf;                  // optional scratch for the tiled 4ph path (W per (λ, q')); may be NULL
+    size_t wbuf_bytes;
 };
 
 // launchers (stream-ordered; return cudaGetLastError())
-cudaError_t launch_rates3(const Tables &t, const RateArgs &a, int ch, int fp64, cudaStream_t s);
-cudaError_t launch_rates4(const Tables &t, const RateArgs &a, int ch, int fp64, int threads,
+// each rate launcher records in a.n_part[ch] how many partial slots per mode it writes
+cudaError_t launch_rates3(const Tables &t, RateArgs &a, int ch, int fp64, cudaStream_t s);
+cudaError_t launch_rates4(const Tables &t, RateArgs &a, int ch, int fp64, int threads,
                           cudaStream_t s);
+// bytes of W scratch the tiled 4ph path needs per mode (0 if the general kernel is used)
+size_t rates4_wbuf_per_mode(const Tables &t, int fp64);
 cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3,
                           double c4, double *gamma, double *wp, long long *counts,
                           unsigned long long *stats, cudaStream_t s);
@@ -77,9 +84,9 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
                             const double *c2_R, const double *c2_phi, const double *c2_ism,
                             double eig_to_w2, double *om, double *vel, double2 *ev, double *eig,
                             int *err, cudaStream_t s);
-cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float2 *ev32,
-                               const double2 *ev, unsigned *vmask, double *invw, float *invw32,
-                               cudaStream_t s);
+cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
+                               float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
+                               float *invw32, cudaStream_t s);
 cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ, float *occ32,
                                cudaStream_t s);
 cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4, float2 *P4_32,

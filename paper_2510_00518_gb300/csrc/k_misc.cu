@@ -174,7 +174,7 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
 
 // ------------------------------------------------------------------------------ tables
 
-__global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float2 *ev32,
+__global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float *om32lo, float2 *ev32,
                                    const double2 *ev, unsigned *vmask, double *invw, float *invw32) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nm = (long long)N * nb;
@@ -183,6 +183,7 @@ __global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float
         if (q == 0 && j < 3) om[i] = 0.0;
         const double w = om[i];
         om32[i] = (float)w;
+        om32lo[i] = (float)(w - (double)(float)w);
         invw[i] = w > 0.0 ? 1.0 / w : 0.0;
         invw32[i] = w > 0.0 ? (float)(1.0 / w) : 0.0f;
     }
@@ -198,12 +199,12 @@ __global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float
     }
 }
 
-cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float2 *ev32,
-                               const double2 *ev, unsigned *vmask, double *invw, float *invw32,
-                               cudaStream_t s) {
+cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
+                               float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
+                               float *invw32, cudaStream_t s) {
     const long long n = (long long)t.N * t.nb * t.nb;
-    mode_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.N, t.nb, om, om32, ev32, ev,
-                                                                    vmask, invw, invw32);
+    mode_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.N, t.nb, om, om32, om32lo, ev32,
+                                                                    ev, vmask, invw, invw32);
     return cudaGetLastError();
 }
 
@@ -244,9 +245,11 @@ cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4,
 
 // ------------------------------------------------------------------------------ reduction
 
+struct int5 { int a, b, c, d, e; };
+
 // One warp per (channel, mode): lane l sums q' = l, l + 32, ... in order, then a fixed
 // butterfly; Γ = C / N^k * Σ, WP = Σ / N^k (k = 1 for 3ph, 2 for 4ph).
-__global__ void reduce_kernel(int n_modes, int N, int channel_mask, double c3, double c4,
+__global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask, double c3, double c4,
                               const double *part_g, const double *part_wp, const long long *part_n,
                               const long long *part_items, double *gamma, double *wp,
                               long long *counts, unsigned long long *stats) {
@@ -258,7 +261,8 @@ __global__ void reduce_kernel(int n_modes, int N, int channel_mask, double c3, d
     long long n = 0, it = 0;
     if ((channel_mask >> ch) & 1) {
         const size_t base = ((size_t)ch * n_modes + ms) * N;
-        for (int q = lane; q < N; q += 32) {
+        const int np = ch == 0 ? n_part.a : ch == 1 ? n_part.b : ch == 2 ? n_part.c : ch == 3 ? n_part.d : n_part.e;
+        for (int q = lane; q < np; q += 32) {
             g += part_g[base + q];
             p += part_wp[base + q];
             n += part_n[base + q];
@@ -290,8 +294,10 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
                           unsigned long long *stats, cudaStream_t s) {
     const long long threads = 32LL * 5 * a.n_modes;
     if (threads == 0) return cudaSuccess;
+    int5 np;
+    np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
     reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        a.n_modes, t.N, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, gamma,
+        a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, gamma,
         wp, counts, stats);
     return cudaGetLastError();
 }

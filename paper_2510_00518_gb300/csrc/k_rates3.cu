@@ -90,8 +90,9 @@ static cudaError_t launch3(const Tables &t, const RateArgs &a, int ch, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_rates3(const Tables &t, const RateArgs &a, int ch, int fp64, cudaStream_t s) {
+cudaError_t launch_rates3(const Tables &t, RateArgs &a, int ch, int fp64, cudaStream_t s) {
     (void)fp64;
+    a.n_part[ch] = t.N;
     switch (t.n_atoms) {
     case 1: return launch3<1>(t, a, ch, s);
     case 2: return launch3<2>(t, a, ch, s);

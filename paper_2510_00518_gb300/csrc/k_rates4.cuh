@@ -59,20 +59,98 @@ static __device__ __noinline__ bool window_exact4(int ch, double w0, double w1, 
 // symmetry factor of the 4ph channels: 1/2 (++, +-), 1/6 (--)
 template <typename R> __device__ __forceinline__ R sym4(int ch) { return ch == 4 ? R(1) / R(6) : R(0.5); }
 
+constexpr int kQChunk = 1024;      // partner q'' handled per compaction round
+
+// Error-free sum: a + b = s + e exactly (Knuth's TwoSum, round-to-nearest FP32).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// Δ = ω + s1 ω' + s2 ω'' - ω''' from hi/lo FP32 splits of each ω (|error| ~ 2^-44 ω_max): the
+// Gaussian's argument in the mixed path without FP64 instructions.
+__device__ __forceinline__ float delta_comp(float h0, float l0, float h1, float l1, float h2, float l2,
+                                            float h3, float l3, int s1, int s2) {
+    float e1, e2, e3;
+    const float x1 = two_sum(h0, (float)s1 * h1, e1);
+    const float x2 = two_sum(x1, (float)s2 * h2, e2);
+    const float x3 = two_sum(x2, -h3, e3);
+    const float lo = ((l0 + (float)s1 * l1) + ((float)s2 * l2 - l3));
+    return x3 + ((e1 + e2) + (e3 + lo));
+}
+
+// Window masks of one q'': bit j'' of mask[j'''] is set iff the process is kept.  FP32 prefilter
+// with the proven bound; candidates inside the band are decided by the exact FP64 Δ.
+template <int NB>
+__device__ __forceinline__ int window_masks(const Tables &t, const RateArgs &a, int ch, int s2,
+                                            float base32, double w0, double w1, int q2, int q3,
+                                            unsigned (&mask)[NB]) {
+    const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+    float t2[NB], w3f[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        t2[j] = base32 + (float)s2 * t.om32[q2 * NB + j];
+        w3f[j] = t.om32[q3 * NB + j];
+    }
+    int n = 0;
+#pragma unroll
+    for (int j3 = 0; j3 < NB; ++j3) {
+        unsigned m = 0;
+        if ((v3 >> j3) & 1u) {
+#pragma unroll
+            for (int j2 = 0; j2 < NB; ++j2) {
+                if (!((v2 >> j2) & 1u)) continue;
+                const float ad = fabsf(t2[j2] - w3f[j3]);
+                bool keep;
+                if (ad <= a.lo32) keep = true;
+                else if (ad > a.hi32) keep = false;
+                else keep = window_exact4(ch, w0, w1, t.om[q2 * NB + j2], t.om[q3 * NB + j3], a.two_sigma);
+                m |= (unsigned)keep << j2;
+            }
+        }
+        mask[j3] = m;
+        n += (m != 0);
+    }
+    return n;
+}
+
+// Kahan-compensated FP32 accumulator (mixed path) / plain FP64 accumulator (FP64 path).
+template <typename R> struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(R x) { s += (double)x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <typename R, int NA>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 4)
 rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
+    // X-route (FP32, <= 2 atoms): X[c,d][γδ] = Σ_r P_r W_r[γδ] once per q'', then 36 complex
+    // MACs per (q'', j''') item.  Otherwise Y[cγ] is contracted key by key per item.
+    constexpr bool XROUTE = (sizeof(R) == 4) && (NA <= 2);
     const int s1 = (ch == 4) ? -1 : 1;
     const int s2 = (ch == 2) ? 1 : -1;
     const int N = t.N;
 
     extern __shared__ __align__(16) unsigned char smem[];
     C *sW = reinterpret_cast<C *>(smem);                        // [n_keys * 9]
-    C *sE = sW + t.n_keys * 9;                                  // [NA*NA*9]  e_λ(aα) e^s1_λ'(bβ)
+    C *sCon = sW + t.n_keys * 9;                                // [nc4 * 9]  per-cluster terms
+    C *sE = sCon + t.nc4 * 9;                                   // [NA*NA*9]  e_λ(aα) e^s1_λ'(bβ)
     C *se0 = sE + NA * NA * 9;                                  // [NB]       e_λ
-    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(se0 + NB + (NB & 1));  // [blockDim * NB]
+    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(se0 + NB + (NB & 1));  // [kQChunk]
     __shared__ int s_scan[32];
     __shared__ double s_red[32];
     __shared__ long long s_redn[32];
@@ -89,7 +167,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const R *occ = Sel<R>::occ(t);
     const R *invw = Sel<R>::invw(t);
 
-    double acc_g = 0.0, acc_wp = 0.0;
+    Acc<R> acc_g, acc_wp;
     long long acc_n = 0, acc_items = 0;
 
     const bool active = !(q0 == 0 && j0 < 3);
@@ -104,7 +182,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
         for (int j1 = 0; j1 < NB; ++j1) {
             if (!((vm1 >> j1) & 1u)) continue;
             const int m1 = q1 * NB + j1;
-            __syncthreads();                       // previous j1 finished with sW / sE / sQ
+            __syncthreads();                       // previous j1 finished with the shared tables
             for (int k = threadIdx.x; k < NA * NA * 9; k += blockDim.x) {
                 const int ab = k / 9, ij = k - ab * 9;
                 const int at = ab / NA, bt = ab - at * NA;
@@ -113,148 +191,187 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                 sE[k] = cmul(se0[3 * at + al], y);
             }
             __syncthreads();
-            // W_r[γδ], one entry per thread; clusters of a key summed in order (deterministic)
+            // per-cluster terms exp(-i q.R3 + i s1 q'.(R1 - R3)) / sqrt(m) Σ_αβ Φ[αβγδ] E[αβ]
+            for (int k = threadIdx.x; k < t.nc4 * 9; k += blockDim.x) {
+                const int c = k / 9, gd = k - c * 9;
+                const int4 at = t.c4_at[c];
+                const int idx = mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) -
+                                            phase_index(c0, t.c4_r3[c], t.L), t.L);
+                const R *ph4 = phi4 + 81 * c + gd;
+                const C *E = sE + (at.x * NA + at.y) * 9;
+                C v = czero<C>();
+#pragma unroll
+                for (int ab = 0; ab < 9; ++ab) v = crfma(ph4[9 * ab], E[ab], v);
+                const C p = cmul(rt[idx], v);
+                sCon[k] = cmake(p.x * ism4[c], p.y * ism4[c]);
+            }
+            __syncthreads();
+            // W_r[γδ]: clusters of a key summed in order (deterministic)
             for (int k = threadIdx.x; k < t.n_keys * 9; k += blockDim.x) {
                 const int r = k / 9, gd = k - r * 9;
                 C acc = czero<C>();
-                for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c) {
-                    const int4 at = t.c4_at[c];
-                    const int idx = mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) -
-                                                phase_index(c0, t.c4_r3[c], t.L), t.L);
-                    const R *ph4 = phi4 + 81 * c + gd;
-                    const C *E = sE + (at.x * NA + at.y) * 9;
-                    C s = czero<C>();
-#pragma unroll
-                    for (int ab = 0; ab < 9; ++ab) s = crfma(ph4[9 * ab], E[ab], s);
-                    acc = crfma(ism4[c], cmul(rt[idx], s), acc);
-                }
+                for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c) acc = cadd(acc, sCon[c * 9 + gd]);
                 sW[k] = acc;
             }
             __syncthreads();
 
             const float base32 = w0f + (float)s1 * t.om32[m1];
             const double w1 = t.om[m1];
-            for (int q2base = 0; q2base < N; q2base += blockDim.x) {
-                const int q2 = q2base + threadIdx.x;
-                unsigned mask[NB];
-                int n_items = 0;
-                if (q2 < N) {
+            for (int qb = 0; qb < N; qb += kQChunk) {
+                const int qe = min(N, qb + kQChunk);
+                // pass 1: window masks of this thread's q''; the X-route keeps those with a kept
+                // process in a small local list (q'' packed with the 36 mask bits) and counts them
+                constexpr int kPer = kQChunk / 64;              // blockDim >= 64
+                unsigned long long ent[XROUTE ? kPer : 1];
+                int n_act = 0;
+                for (int q2 = qb + threadIdx.x; q2 < qe; q2 += blockDim.x) {
                     const int4 c2 = t.qc[q2];
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
-                    const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
-                    float t2[NB], w3f[NB];
+                    unsigned mask[NB];
+                    if (window_masks<NB>(t, a, ch, s2, base32, w0, w1, q2, q3, mask) > 0) {
+                        if constexpr (XROUTE) {
+                            unsigned long long e = (unsigned long long)q2 << 40;
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        t2[j] = base32 + (float)s2 * t.om32[q2 * NB + j];
-                        w3f[j] = t.om32[q3 * NB + j];
-                    }
-#pragma unroll
-                    for (int j3 = 0; j3 < NB; ++j3) {
-                        unsigned m = 0;
-                        if ((v3 >> j3) & 1u) {
-#pragma unroll
-                            for (int j2 = 0; j2 < NB; ++j2) {
-                                if (!((v2 >> j2) & 1u)) continue;
-                                const float ad = fabsf(t2[j2] - w3f[j3]);
-                                bool keep;
-                                if (ad <= a.lo32) keep = true;
-                                else if (ad > a.hi32) keep = false;
-                                else keep = window_exact4(ch, w0, w1, t.om[q2 * NB + j2],
-                                                          t.om[q3 * NB + j3], a.two_sigma);
-                                m |= (unsigned)keep << j2;
-                            }
+                            for (int j3 = 0; j3 < NB; ++j3) e |= (unsigned long long)mask[j3] << (NB * j3);
+                            ent[n_act] = e;
                         }
-                        mask[j3] = m;
-                        n_items += (m != 0);
+                        ++n_act;
                     }
-                } else {
-#pragma unroll
-                    for (int j3 = 0; j3 < NB; ++j3) mask[j3] = 0;
                 }
                 int total;
-                int off = block_exclusive_scan(n_items, s_scan, &total);
-#pragma unroll
-                for (int j3 = 0; j3 < NB; ++j3)
-                    if (mask[j3])
-                        sQ[off++] = ((unsigned long long)q2 << 32) | ((unsigned long long)j3 << 24) | mask[j3];
+                int off = block_exclusive_scan(n_act, s_scan, &total);
+                // pass 2: write them in order
+                if constexpr (XROUTE) {
+                    for (int k = 0; k < n_act; ++k) sQ[off + k] = ent[k];
+                } else if (n_act) {
+                    for (int q2 = qb + threadIdx.x; q2 < qe; q2 += blockDim.x) {
+                        const int4 c2 = t.qc[q2];
+                        const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                               t.mesh[0], t.mesh[1], t.mesh[2]);
+                        unsigned mask[NB];
+                        if (window_masks<NB>(t, a, ch, s2, base32, w0, w1, q2, q3, mask) > 0) sQ[off++] = q2;
+                    }
+                }
                 __syncthreads();
 
                 for (int it = threadIdx.x; it < total; it += blockDim.x) {
-                    ++acc_items;
-                    const unsigned long long item = sQ[it];
-                    const int iq2 = (int)(item >> 32);
-                    const int j3 = (int)((item >> 24) & 0xff);
-                    unsigned m = (unsigned)(item & 0xffffffu);
+                    const unsigned long long e = sQ[it];
+                    const int iq2 = XROUTE ? (int)(e >> 40) : (int)e;
                     const int4 c2 = t.qc[iq2];
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
-                    // Y[cγ] = Σ_d Σ_{r in (c,d)} P_r^s2 Σ_δ W_r[γδ] e*_λ'''(dδ)
-                    C Y[NA][3];
+                    unsigned mask[NB];
+                    if constexpr (XROUTE) {
 #pragma unroll
-                    for (int c = 0; c < NA; ++c)
-#pragma unroll
-                        for (int g = 0; g < 3; ++g) Y[c][g] = czero<C>();
-                    const C *P = P4 + (size_t)iq2 * t.n_keys;
-#pragma unroll
-                    for (int c = 0; c < NA; ++c) {
-#pragma unroll
-                        for (int d = 0; d < NA; ++d) {
-                            const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
-                            if (r0 == r1) continue;
-                            C e3[3];
-#pragma unroll
-                            for (int dl = 0; dl < 3; ++dl)
-                                e3[dl] = cconj(ev[(q3 * NB + 3 * d + dl) * NB + j3]);
-                            for (int r = r0; r < r1; ++r) {
-                                const C ph = cconj_if(P[r], s2 < 0);
-                                const C *Wr = sW + 9 * r;
-#pragma unroll
-                                for (int g = 0; g < 3; ++g) {
-                                    C u = cmul(Wr[3 * g], e3[0]);
-                                    u = cfma(Wr[3 * g + 1], e3[1], u);
-                                    u = cfma(Wr[3 * g + 2], e3[2], u);
-                                    Y[c][g] = cfma(ph, u, Y[c][g]);
-                                }
-                            }
-                        }
+                        for (int j3 = 0; j3 < NB; ++j3) mask[j3] = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);
+                    } else {
+                        window_masks<NB>(t, a, ch, s2, base32, w0, w1, iq2, q3, mask);
                     }
-                    const int m3 = q3 * NB + j3;
-                    const double w3 = t.om[m3];
-                    const R n3 = occ[m3], iw3 = invw[m3];
-                    while (m) {
-                        const int j2 = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int m2 = iq2 * NB + j2;
-                        C V = czero<C>();
+                    const C *P = P4 + (size_t)iq2 * t.n_keys;
+                    C X[XROUTE ? NA : 1][XROUTE ? NA : 1][9];
+                    if constexpr (XROUTE) {
 #pragma unroll
                         for (int c = 0; c < NA; ++c)
 #pragma unroll
-                            for (int g = 0; g < 3; ++g)
-                                V = cfma(cconj_if(ev[(iq2 * NB + 3 * c + g) * NB + j2], s2 < 0), Y[c][g], V);
-                        const double d = delta_exact(ch, w0, w1, t.om[m2], w3);
-                        R w;
-                        if constexpr (sizeof(R) == 8) {
-                            const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
-                            w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
-                                g * invw[m0] * invw[m1] * invw[m2] * iw3;
+                            for (int d = 0; d < NA; ++d) {
+#pragma unroll
+                                for (int k = 0; k < 9; ++k) X[c][d][k] = czero<C>();
+                                const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
+                                for (int r = r0; r < r1; ++r) {
+                                    const C ph = cconj_if(P[r], s2 < 0);
+                                    const C *Wr = sW + 9 * r;
+#pragma unroll
+                                    for (int k = 0; k < 9; ++k) X[c][d][k] = cfma(ph, Wr[k], X[c][d][k]);
+                                }
+                            }
+                    }
+#pragma unroll 1
+                    for (int j3 = 0; j3 < NB; ++j3) {
+                        unsigned m = mask[j3];
+                        if (!m) continue;
+                        ++acc_items;
+                        C Y[NA][3];
+#pragma unroll
+                        for (int c = 0; c < NA; ++c)
+#pragma unroll
+                            for (int g = 0; g < 3; ++g) Y[c][g] = czero<C>();
+                        if constexpr (XROUTE) {
+                            // Y[cγ] = Σ_dδ X[c,d][γδ] e*_λ'''(dδ)
+#pragma unroll
+                            for (int d = 0; d < NA; ++d) {
+                                C e3[3];
+#pragma unroll
+                                for (int dl = 0; dl < 3; ++dl) e3[dl] = cconj(ev[(q3 * NB + 3 * d + dl) * NB + j3]);
+#pragma unroll
+                                for (int c = 0; c < NA; ++c)
+#pragma unroll
+                                    for (int g = 0; g < 3; ++g)
+#pragma unroll
+                                        for (int dl = 0; dl < 3; ++dl) Y[c][g] = cfma(X[c][d][3 * g + dl], e3[dl], Y[c][g]);
+                            }
                         } else {
-                            const float df = (float)d;
-                            const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
-                            w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
-                                (invw[m0] * invw[m1]) * (invw[m2] * iw3);
+                            // Y[cγ] = Σ_d Σ_{r in (c,d)} P_r^s2 Σ_δ W_r[γδ] e*_λ'''(dδ)
+#pragma unroll
+                            for (int c = 0; c < NA; ++c) {
+#pragma unroll
+                                for (int d = 0; d < NA; ++d) {
+                                    const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
+                                    if (r0 == r1) continue;
+                                    C e3[3];
+#pragma unroll
+                                    for (int dl = 0; dl < 3; ++dl) e3[dl] = cconj(ev[(q3 * NB + 3 * d + dl) * NB + j3]);
+                                    for (int r = r0; r < r1; ++r) {
+                                        const C ph = cconj_if(P[r], s2 < 0);
+                                        const C *Wr = sW + 9 * r;
+#pragma unroll
+                                        for (int g = 0; g < 3; ++g) {
+                                            C u = cmul(Wr[3 * g], e3[0]);
+                                            u = cfma(Wr[3 * g + 1], e3[1], u);
+                                            u = cfma(Wr[3 * g + 2], e3[2], u);
+                                            Y[c][g] = cfma(ph, u, Y[c][g]);
+                                        }
+                                    }
+                                }
+                            }
                         }
-                        acc_wp += (double)w;
-                        acc_g += (double)w * cabs2(V);
-                        acc_n += 1;
+                        const int m3 = q3 * NB + j3;
+                        const R n3 = occ[m3], iw3 = invw[m3];
+                        while (m) {
+                            const int j2 = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int m2 = iq2 * NB + j2;
+                            C V = czero<C>();
+#pragma unroll
+                            for (int c = 0; c < NA; ++c)
+#pragma unroll
+                                for (int g = 0; g < 3; ++g)
+                                    V = cfma(cconj_if(ev[(iq2 * NB + 3 * c + g) * NB + j2], s2 < 0), Y[c][g], V);
+                            R w;
+                            if constexpr (sizeof(R) == 8) {
+                                const double d = delta_exact(ch, w0, w1, t.om[m2], t.om[m3]);
+                                const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                                w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
+                                    g * invw[m0] * invw[m1] * invw[m2] * iw3;
+                            } else {
+                                const float df = delta_comp(t.om32[m0], t.om32lo[m0], t.om32[m1], t.om32lo[m1],
+                                                            t.om32[m2], t.om32lo[m2], t.om32[m3], t.om32lo[m3], s1, s2);
+                                const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
+                                w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
+                                    (invw[m0] * invw[m1]) * (invw[m2] * iw3);
+                            }
+                            acc_wp.add(w);
+                            acc_g.add(w * (V.x * V.x + V.y * V.y));
+                            acc_n += 1;
+                        }
                     }
                 }
                 __syncthreads();                   // sQ reused by the next chunk
             }
         }
     }
-    const double g = block_sum(acc_g, s_red);
-    const double wp = block_sum(acc_wp, s_red);
+    const double g = block_sum(acc_g.value(), s_red);
+    const double wp = block_sum(acc_wp.value(), s_red);
     const long long n = block_sum(acc_n, s_redn);
     const long long ni = block_sum(acc_items, s_redn);
     if (threadIdx.x == 0) {
@@ -270,8 +387,8 @@ template <typename R, int NA>
 cudaError_t launch4(const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
-    size_t smem = sizeof(C) * ((size_t)t.n_keys * 9 + NA * NA * 9 + NB + (NB & 1)) +
-                  sizeof(unsigned long long) * (size_t)threads * NB;
+    size_t smem = sizeof(C) * ((size_t)t.n_keys * 9 + (size_t)t.nc4 * 9 + NA * NA * 9 + NB) +
+                  sizeof(C) + sizeof(unsigned long long) * (size_t)kQChunk;
     smem = (smem + 15) & ~size_t(15);
     cudaError_t e = cudaFuncSetAttribute(rates4_kernel<R, NA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

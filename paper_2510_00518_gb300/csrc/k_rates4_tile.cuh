@@ -1,0 +1,343 @@
+// k_rates4_tile.cuh - four-phonon path for small cells (<= 2 atoms), in two kernels.
+//
+// w4_kernel writes W_r[γδ](λ, q', j') for every partner branch j' of a unit (λ, q') to a global
+// buffer (HBM is otherwise idle here; one pass over the clusters per unit).  rates4_tile_kernel
+// then owns the unit: it copies that W to shared memory, sweeps q'' in rounds of 128 (one per
+// thread), tests the window against every j' at once (branch-free FP32 prefilter, rare
+// ambiguous candidates decided by the exact FP64 Δ), compacts the (q'', j', masks) entries with
+// a block scan, and evaluates them:
+//   FP32: X[c,d][γδ] = Σ_{r in (c,d)} P_r^s2 W_r[γδ] once per entry, Y = X e*''' per j''' (36 MACs);
+//   FP64: Y[cγ] = Σ_r P_r^s2 Σ_δ W_r[γδ] e*'''(dδ) per j''' (register-light).
+// The same window decision, weights and accumulation as the general kernel (k_rates4.cuh).
+#pragma once
+#include "k_rates4.cuh"
+
+namespace fc4 {
+
+constexpr int kTileQ = 128;
+
+__host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; }
+
+
+// W[j'][r][γδ] of units (λ, q') for every partner branch j', written to global memory (layout
+// [unit][j'][r][γδ]).  One block per (λ, group of kW4Group q'): Φ contracted with e_λ and the mass
+// factor, Φ~_c[β][γδ] = Σ_α Φ_c[αβγδ] e_λ(aα) / sqrt(m), is built once in shared memory; then per
+// q' W_r = Σ_{c in r} exp(i(s1 q'.(R1 - R3) - q.R3)) Σ_β e^s1_λ'(bβ) Φ~_c[β][γδ], clusters of a key
+// summed in a fixed order, entries ordered key-major so that a warp shares one cluster range.
+constexpr int kW4Group = 8;
+
+template <typename R, int NA>
+__global__ void __launch_bounds__(128)
+w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch, int mode0,
+          Cplx<R> *wout) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    const int s1 = (ch == 4) ? -1 : 1;
+    const int N = t.N, nk = t.n_keys, nc4 = t.nc4;
+    const int ngrp = (N + kW4Group - 1) / kW4Group;
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *sPt = reinterpret_cast<C *>(smem);                       // [nc4][3][9]
+    C *sPh = sPt + nc4 * 27;                                    // [nc4]
+    C *sE1 = sPh + nc4;                                         // [NB][NB]  e^s1_λ'(comp) per j'
+    C *se0 = sE1 + NB * NB;                                     // [NB]
+    const int ml = blockIdx.x / ngrp, qg = blockIdx.x - ml * ngrp;
+    const int m0 = a.modes[mode0 + ml];
+    const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+    const C *ev = Sel<R>::ev(t);
+    const C *rt = Sel<R>::rt(t);
+    const R *phi4 = Sel<R>::phi4(t);
+    const R *ism4 = Sel<R>::ism4(t);
+    const int4 c0 = t.qc[q0];
+    for (int k = threadIdx.x; k < NB; k += blockDim.x) se0[k] = ev[(q0 * NB + k) * NB + j0];
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc4 * 27; k += blockDim.x) {
+        const int c = k / 27, rem = k - c * 27;
+        const int be = rem / 9, gd = rem - be * 9;
+        const int a0 = t.c4_at[c].x;
+        const R *ph4 = phi4 + 81 * c + be * 9 + gd;
+        C v = czero<C>();
+#pragma unroll
+        for (int al = 0; al < 3; ++al) v = crfma(ph4[27 * al], se0[3 * a0 + al], v);
+        sPt[k] = cmake(v.x * ism4[c], v.y * ism4[c]);
+    }
+    const int q1_end = min(N, (qg + 1) * kW4Group);
+    for (int q1 = qg * kW4Group; q1 < q1_end; ++q1) {
+        const int4 c1 = t.qc[q1];
+        __syncthreads();                                         // sPt ready / previous q' done
+        for (int c = threadIdx.x; c < nc4; c += blockDim.x)
+            sPh[c] = rt[mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) - phase_index(c0, t.c4_r3[c], t.L), t.L)];
+        for (int k = threadIdx.x; k < NB * NB; k += blockDim.x) {
+            const int j1 = k / NB, comp = k - j1 * NB;
+            sE1[k] = cconj_if(ev[(q1 * NB + comp) * NB + j1], s1 < 0);
+        }
+        __syncthreads();
+        C *wo = wout + ((size_t)ml * N + q1) * NB * nk * 9;
+        for (int k = threadIdx.x; k < nk * NB * 9; k += blockDim.x) {
+            const int r = k / (NB * 9), rem = k - r * (NB * 9);
+            const int j1 = rem / 9, gd = rem - j1 * 9;
+            C acc = czero<C>();
+            for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c) {
+                const int b = t.c4_at[c].y;
+                const C *pt = sPt + c * 27 + gd;
+                const C *e1 = sE1 + j1 * NB + 3 * b;
+                C v = cmul(e1[0], pt[0]);
+                v = cfma(e1[1], pt[9], v);
+                v = cfma(e1[2], pt[18], v);
+                acc = cfma(sPh[c], v, acc);
+            }
+            wo[(j1 * nk + r) * 9 + gd] = acc;
+        }
+    }
+}
+
+template <typename R, int NA>
+__global__ void __launch_bounds__(kTileQ, 4)
+rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
+                   int mode0, const Cplx<R> *__restrict__ wall) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    constexpr bool XROUTE = (sizeof(R) == 4);
+    const int s1 = (ch == 4) ? -1 : 1;
+    const int s2 = (ch == 2) ? 1 : -1;
+    const int N = t.N, nk = t.n_keys;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *sW = reinterpret_cast<C *>(smem);                        // [NB][nk][9]
+    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB]
+    __shared__ int s_scan[32];
+    __shared__ double s_red[32];
+    __shared__ long long s_redn[32];
+
+    const int unit = blockIdx.x;                                // (mode - mode0) * N + q'
+    const int ml = unit / N, q1 = unit - ml * N;
+    const int ms = mode0 + ml;
+    const int m0 = a.modes[ms];
+    const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+    const C *ev = Sel<R>::ev(t);
+    const C *P4 = Sel<R>::P4(t);
+    const R *occ = Sel<R>::occ(t);
+    const R *invw = Sel<R>::invw(t);
+
+    Acc<R> acc_g, acc_wp;
+    long long acc_n = 0, acc_items = 0;
+    const unsigned vm1 = t.vmask[q1];
+
+    if (!(q0 == 0 && j0 < 3) && vm1) {
+        const int4 c0 = t.qc[q0], c1 = t.qc[q1];
+        const int b0 = c0.x + s1 * c1.x, b1 = c0.y + s1 * c1.y, b2 = c0.z + s1 * c1.z;
+        const double w0 = t.om[m0];
+        const float w0f = t.om32[m0];
+        {                                                        // W of (λ, q') for every j'
+            const C *src = wall + (size_t)unit * (NB * nk * 9);
+            for (int k = threadIdx.x; k < NB * nk * 9; k += kTileQ) sW[k] = src[k];
+        }
+        float base32[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) base32[j] = w0f + (float)s1 * t.om32[q1 * NB + j];
+
+        for (int qb = 0; qb < N; qb += kTileQ) {
+            const int q2 = qb + threadIdx.x;
+            // window: this thread's q'' against every partner branch j'
+            int n_ent = 0;
+            unsigned long long ent[NB];
+            if (q2 < N) {
+                const int4 c2 = t.qc[q2];
+                const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                       t.mesh[0], t.mesh[1], t.mesh[2]);
+                const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+                float w2f[NB], w3f[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    w2f[j] = (float)s2 * t.om32[q2 * NB + j];
+                    w3f[j] = t.om32[q3 * NB + j];
+                }
+#pragma unroll 1
+                for (int j1 = 0; j1 < NB; ++j1) {
+                    if (!((vm1 >> j1) & 1u)) continue;
+                    const float b = base32[j1];
+                    unsigned long long sure = 0, amb = 0;
+#pragma unroll
+                    for (int j3 = 0; j3 < NB; ++j3)
+#pragma unroll
+                        for (int j2 = 0; j2 < NB; ++j2) {
+                            const float ad = fabsf((b + w2f[j2]) - w3f[j3]);
+                            const bool ok = ((v3 >> j3) & (v2 >> j2) & 1u) != 0;
+                            sure |= (unsigned long long)(ok && ad <= a.lo32) << (NB * j3 + j2);
+                            amb |= (unsigned long long)(ok && ad > a.lo32 && ad <= a.hi32) << (NB * j3 + j2);
+                        }
+                    while (amb) {                                // rare: exact FP64 decision
+                        const int k = __ffsll(amb) - 1;
+                        amb &= amb - 1;
+                        const int j3 = k / NB, j2 = k - j3 * NB;
+                        if (window_exact4(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], t.om[q3 * NB + j3],
+                                          a.two_sigma))
+                            sure |= 1ull << k;
+                    }
+                    if (sure)
+                        ent[n_ent++] = ((unsigned long long)threadIdx.x << 48) |
+                                       ((unsigned long long)j1 << 40) | sure;
+                }
+            }
+            int total;
+            const int off = block_exclusive_scan(n_ent, s_scan, &total);
+            for (int k = 0; k < n_ent; ++k) sQ[off + k] = ent[k];
+            __syncthreads();
+
+            for (int it = threadIdx.x; it < total; it += kTileQ) {
+                const unsigned long long e = sQ[it];
+                const int iq2 = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
+                const int4 cc2 = t.qc[iq2];
+                const int iq3 = q_index(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
+                                        t.mesh[0], t.mesh[1], t.mesh[2]);
+                const int m1 = q1 * NB + j1;
+                const C *Prow = P4 + (size_t)iq2 * nk;
+                const C *Wj = sW + j1 * nk * 9;
+                C X[XROUTE ? NA : 1][XROUTE ? NA : 1][9];
+                if constexpr (XROUTE) {
+#pragma unroll
+                    for (int c = 0; c < NA; ++c)
+#pragma unroll
+                        for (int d = 0; d < NA; ++d) {
+#pragma unroll
+                            for (int k = 0; k < 9; ++k) X[c][d][k] = czero<C>();
+                            const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
+                            for (int r = r0; r < r1; ++r) {
+                                const C ph = cconj_if(Prow[r], s2 < 0);
+                                const C *Wr = Wj + 9 * r;
+#pragma unroll
+                                for (int k = 0; k < 9; ++k) X[c][d][k] = cfma(ph, Wr[k], X[c][d][k]);
+                            }
+                        }
+                }
+#pragma unroll 1
+                for (int j3 = 0; j3 < NB; ++j3) {
+                    unsigned m = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);
+                    if (!m) continue;
+                    ++acc_items;
+                    C Y[NA][3];
+#pragma unroll
+                    for (int c = 0; c < NA; ++c)
+#pragma unroll
+                        for (int g = 0; g < 3; ++g) Y[c][g] = czero<C>();
+#pragma unroll
+                    for (int d = 0; d < NA; ++d) {
+                        C e3[3];
+#pragma unroll
+                        for (int dl = 0; dl < 3; ++dl) e3[dl] = cconj(ev[(iq3 * NB + 3 * d + dl) * NB + j3]);
+                        if constexpr (XROUTE) {
+#pragma unroll
+                            for (int c = 0; c < NA; ++c)
+#pragma unroll
+                                for (int g = 0; g < 3; ++g)
+#pragma unroll
+                                    for (int dl = 0; dl < 3; ++dl) Y[c][g] = cfma(X[c][d][3 * g + dl], e3[dl], Y[c][g]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < NA; ++c) {
+                                const int r0 = t.grp_start[c * NA + d], r1 = t.grp_start[c * NA + d + 1];
+                                for (int r = r0; r < r1; ++r) {
+                                    const C ph = cconj_if(Prow[r], s2 < 0);
+                                    const C *Wr = Wj + 9 * r;
+#pragma unroll
+                                    for (int g = 0; g < 3; ++g) {
+                                        C u = cmul(Wr[3 * g], e3[0]);
+                                        u = cfma(Wr[3 * g + 1], e3[1], u);
+                                        u = cfma(Wr[3 * g + 2], e3[2], u);
+                                        Y[c][g] = cfma(ph, u, Y[c][g]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    const int m3 = iq3 * NB + j3;
+                    const R n3 = occ[m3], iw3 = invw[m3];
+                    while (m) {
+                        const int j2 = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int m2 = iq2 * NB + j2;
+                        C V = czero<C>();
+#pragma unroll
+                        for (int c = 0; c < NA; ++c)
+#pragma unroll
+                            for (int g = 0; g < 3; ++g)
+                                V = cfma(cconj_if(ev[(iq2 * NB + 3 * c + g) * NB + j2], s2 < 0), Y[c][g], V);
+                        R w;
+                        if constexpr (sizeof(R) == 8) {
+                            const double d = delta_exact(ch, w0, t.om[m1], t.om[m2], t.om[m3]);
+                            const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                            w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
+                                g * invw[m0] * invw[m1] * invw[m2] * iw3;
+                        } else {
+                            const float df = delta_comp(t.om32[m0], t.om32lo[m0], t.om32[m1], t.om32lo[m1],
+                                                        t.om32[m2], t.om32lo[m2], t.om32[m3], t.om32lo[m3], s1, s2);
+                            const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
+                            w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
+                                (invw[m0] * invw[m1]) * (invw[m2] * iw3);
+                        }
+                        acc_wp.add(w);
+                        acc_g.add(w * (V.x * V.x + V.y * V.y));
+                        acc_n += 1;
+                    }
+                }
+            }
+            __syncthreads();                                     // sQ reused by the next round
+        }
+    }
+    const double g = block_sum(acc_g.value(), s_red);
+    const double wp = block_sum(acc_wp.value(), s_red);
+    const long long n = block_sum(acc_n, s_redn);
+    const long long ni = block_sum(acc_items, s_redn);
+    if (threadIdx.x == 0) {
+        const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
+        a.part_g[o] = g;
+        a.part_wp[o] = wp;
+        a.part_n[o] = n;
+        a.part_items[o] = ni;
+    }
+}
+
+template <typename R, int NA>
+size_t tile_smem_bytes(const Tables &t) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB;
+    return (b + 15) & ~size_t(15);
+}
+
+// W bytes per mode (all q' and j') for the tiled path
+template <typename R, int NA>
+size_t tile_w_bytes_per_mode(const Tables &t) {
+    return sizeof(Cplx<R>) * (size_t)t.N * 3 * NA * t.n_keys * 9;
+}
+
+// Launch W (global) then the tiled kernel, over mode chunks that fit in the W buffer.
+template <typename R, int NA>
+cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_t s) {
+    using C = Cplx<R>;
+    constexpr int NB = 3 * NA;
+    const size_t smem = tile_smem_bytes<R, NA>(t);
+    cudaError_t e = cudaFuncSetAttribute(rates4_tile_kernel<R, NA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB);
+    e = cudaFuncSetAttribute(w4_kernel<R, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+    if (e != cudaSuccess) return e;
+    const size_t per_mode = tile_w_bytes_per_mode<R, NA>(t);
+    const int chunk = (int)(a.wbuf_bytes / per_mode);
+    if (chunk < 1) return cudaErrorInvalidValue;
+    for (int m = 0; m < a.n_modes; m += chunk) {
+        const int nm = min(chunk, a.n_modes - m);
+        const long long ngrp = (t.N + kW4Group - 1) / kW4Group;
+        w4_kernel<R, NA><<<(unsigned)((long long)nm * ngrp), 128, wsmem, s>>>(t, a, ch, m,
+                                                                              reinterpret_cast<C *>(a.wbuf));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        rates4_tile_kernel<R, NA><<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(
+            t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fc4

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-10)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
 def test_static_scratch_matches_fc4_rates(precision, tol):
     sysm = morse_system(seed=0)
     mesh = (3, 3, 3)

@@ -191,7 +191,7 @@ def run_gpu(args):
 
     def step():
         eng.rates(args.T, args.sigma, 31, out=(g, wp, cnt))
-        eng.kappa(args.T, g.sum(0), out=kap)
+        eng.kappa(args.T, g, 31, out=kap)
 
     for _ in range(args.warmup):
         step()
@@ -279,7 +279,7 @@ def run_gpu(args):
             t1 = time.perf_counter()
             e = Engine(*sysm, mesh, precision=prec, block_threads=args.block_threads)
             g2, wp2, c2 = e.rates(args.T, args.sigma, 31)
-            k2 = e.kappa(args.T, g2.sum(0))
+            k2 = e.kappa(args.T, g2, 31)
             gh[:] = g2.cpu().numpy()
             wph[:] = wp2.cpu().numpy()
             ch_[:] = c2.cpu().numpy()

@@ -154,17 +154,27 @@ fc4_status fc4_processes(fc4_ctx *ctx, int channel, int mode, unsigned long long
                          long long cap, long long *n_out);
 
 /* fc4_kappa - RTA thermal conductivity κ_αβ = 1/(N V_cell) Σ_λ C_λ v_α v_β / Γ_λ (W/(m K)),
- * C_λ = k_B x² n (n + 1), x = ħω / k_B T, over every mode of the mesh with ω > 0 and Γ_λ > 0.
- * gamma_total: device [N*nb] total scattering rate per mode (ps^-1); kappa_out: device [9]. */
-fc4_status fc4_kappa(fc4_ctx *ctx, double T_K, const double *gamma_total, double *kappa_out,
-                     void *stream);
+ * C_λ = k_B x² n (n + 1), x = ħω / k_B T, Γ_λ = Σ of gamma[ch][λ] over the channels in
+ * channel_mask, over every mode of the mesh with ω > 0 and Γ_λ > 0 (Results section: RTA κ).
+ * gamma: device [5][N*nb] in ps^-1 (the layout fc4_rates writes for the whole mesh);
+ * kappa_out: device [9], row-major. */
+fc4_status fc4_kappa(fc4_ctx *ctx, double T_K, const double *gamma, int channel_mask,
+                     double *kappa_out, void *stream);
+
+/* fc4_kappa_backward - dL/dΓ_ch(λ) = Σ_αβ dL/dκ_αβ dκ_αβ/dΓ_λ = -C_λ (v_λ . G v_λ) / (N V_cell Γ_λ²)
+ * (G = dL/dκ, units as fc4_kappa) for every channel in channel_mask, 0 elsewhere and for
+ * skipped modes.  gamma: device [5][N*nb]; dL_dkappa: device [9]; dL_dgamma: device [5][N*nb]. */
+fc4_status fc4_kappa_backward(fc4_ctx *ctx, double T_K, const double *gamma, int channel_mask,
+                              const double *dL_dkappa, double *dL_dgamma, void *stream);
 
 /* fc4_rates_backward - gradient of L = Σ_{ch,i} dL_dgamma[ch][i] Γ_ch(i) with respect to every
  * stored Φ3 and Φ4 entry (entries independent), at fixed modes and σ, for the (T, σ, mask,
- * subset) of the last fc4_rates call:
- *   dL/dΦ_c = Σ_processes g w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
- * dL_dgamma: device [5][n_q*nb]; dphi3: device [nc3][27]; dphi4: device [nc4][81] (overwritten;
- * either may be NULL to skip that order).  Returns FC4_ERR_STATE before any fc4_rates call. */
+ * subset) of the last fc4_rates call, in FP64 whatever the context's precision:
+ *   dL/dΦ_c = Σ_processes dL/dΓ C/N^k w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
+ * Deterministic (fixed summation order).  dL_dgamma: device [5][n_q*nb]; dphi3: device
+ * [nc3][27]; dphi4: device [nc4][81], in the cluster order given to fc4_init (overwritten;
+ * either may be NULL to skip that order).  Cells of at most 2 atoms.  Returns FC4_ERR_STATE
+ * before any fc4_rates call.  Scratch: n_q*nb*max(27 nc3, 81 nc4) doubles (grown on demand). */
 fc4_status fc4_rates_backward(fc4_ctx *ctx, const double *dL_dgamma, double *dphi3,
                               double *dphi4, void *stream);
 

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "CHANNELS", "lib_path"]
+__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "CHANNELS", "lib_path", "rates_fn", "kappa_fn"]
 
 FP64, MIXED = 0, 1
 CHANNELS = ("3ph+", "3ph-", "4ph++", "4ph+-", "4ph--")
@@ -69,7 +69,8 @@ def load(build_if_missing: bool = False):
         "fc4_get_modes": [vp, vp, vp, vp],
         "fc4_rates": [vp, d, i, d, i, vp, i, vp, vp, vp, vp],
         "fc4_processes": [vp, i, i, vp, ll, ctypes.POINTER(ll)],
-        "fc4_kappa": [vp, d, vp, vp, vp],
+        "fc4_kappa": [vp, d, vp, i, vp, vp],
+        "fc4_kappa_backward": [vp, d, vp, i, vp, vp, vp],
         "fc4_rates_backward": [vp, vp, vp, vp, vp],
         "fc4_update_anharmonic": [vp, vp, vp],
         "fc4_info": [vp, vp],
@@ -259,13 +260,26 @@ class Engine:
         self._check(self.lib.fc4_processes(self.ctx, channel, mode, _ptr(out), n.value, ctypes.byref(n)))
         return out[:n.value]
 
-    def kappa(self, T: float, gamma_total, out=None, stream=None):
+    def kappa(self, T: float, gamma, channel_mask: int = 31, out=None, stream=None):
+        """RTA κ (3x3, W/m/K) from Γ of the whole mesh, ``gamma`` [5, N*nb] as written by ``rates``."""
         import torch
-        g = gamma_total.contiguous()
+        g = gamma.contiguous()
         if out is None:
             out = torch.empty(9, dtype=torch.float64, device=g.device)
-        self._check(self.lib.fc4_kappa(self.ctx, float(T), _tptr(g), _tptr(out), _stream(stream)))
+        self._check(self.lib.fc4_kappa(self.ctx, float(T), _tptr(g), int(channel_mask), _tptr(out),
+                                       _stream(stream)))
         return out.view(3, 3)
+
+    def kappa_backward(self, T: float, gamma, dL_dkappa, channel_mask: int = 31, out=None, stream=None):
+        """dL/dΓ [5, N*nb] from dL/dκ (3x3)."""
+        import torch
+        g = gamma.contiguous()
+        dk = dL_dkappa.contiguous().reshape(9)
+        if out is None:
+            out = torch.empty_like(g)
+        self._check(self.lib.fc4_kappa_backward(self.ctx, float(T), _tptr(g), int(channel_mask), _tptr(dk),
+                                                _tptr(out), _stream(stream)))
+        return out
 
     def backward(self, dL_dgamma, dphi3=None, dphi4=None, stream=None):
         import torch
@@ -278,8 +292,66 @@ class Engine:
                                                 _stream(stream)))
         return dphi3, dphi4
 
+    def backward_grads(self, dL_dgamma, stream=None):
+        """(dL/dΦ3, dL/dΦ4) device tensors for the last rates call (alias of ``backward``)."""
+        return self.backward(dL_dgamma, stream=stream)
+
     def update_anharmonic(self, phi3=None, phi4=None):
         p3 = None if phi3 is None else _np(phi3, np.float64)
         p4 = None if phi4 is None else _np(phi4, np.float64)
         self._check(self.lib.fc4_update_anharmonic(self.ctx, None if p3 is None else _ptr(p3),
                                                    None if p4 is None else _ptr(p4)))
+
+
+# ------------------------------------------------------------------------------ autograd
+
+def _autograd():
+    import torch
+
+    class Rates(torch.autograd.Function):
+        """Γ [5, n_modes] as a function of the Φ3 / Φ4 cluster values (modes and σ fixed).
+        Forward: fc4_update_anharmonic + fc4_rates.  Backward: fc4_rates_backward."""
+
+        @staticmethod
+        def forward(ctx, phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset):
+            engine.update_anharmonic(phi3.detach().cpu().numpy(), phi4.detach().cpu().numpy())
+            g, _, _ = engine.rates(T, sigma_thz, channel_mask, q_subset=q_subset)
+            ctx.engine = engine
+            ctx.dev3, ctx.dev4 = phi3.device, phi4.device
+            return g
+
+        @staticmethod
+        def backward(ctx, grad_gamma):
+            d3, d4 = ctx.engine.backward(grad_gamma.contiguous().to(torch.float64))
+            d3 = d3.to(ctx.dev3) if d3 is not None else None
+            d4 = d4.to(ctx.dev4) if d4 is not None else None
+            return d3, d4, None, None, None, None, None
+
+    class Kappa(torch.autograd.Function):
+        """κ (3x3) as a function of Γ [5, N*nb].  Backward: fc4_kappa_backward."""
+
+        @staticmethod
+        def forward(ctx, gamma, engine, T, channel_mask):
+            ctx.save_for_backward(gamma)
+            ctx.engine, ctx.T, ctx.mask = engine, T, channel_mask
+            return engine.kappa(T, gamma, channel_mask).clone()
+
+        @staticmethod
+        def backward(ctx, grad_kappa):
+            (gamma,) = ctx.saved_tensors
+            g = ctx.engine.kappa_backward(ctx.T, gamma, grad_kappa.to(torch.float64), ctx.mask)
+            return g, None, None, None
+
+    return Rates, Kappa
+
+
+def rates_fn(phi3, phi4, engine, T, sigma_thz, channel_mask=31, q_subset=None):
+    """Differentiable Γ(Φ3, Φ4) (see ``_autograd``)."""
+    Rates, _ = _autograd()
+    return Rates.apply(phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset)
+
+
+def kappa_fn(gamma, engine, T, channel_mask=31):
+    """Differentiable κ(Γ) (see ``_autograd``)."""
+    _, Kappa = _autograd()
+    return Kappa.apply(gamma, engine, T, channel_mask)

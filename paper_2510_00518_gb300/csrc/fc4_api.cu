@@ -72,6 +72,11 @@ struct fc4_ctx {
     size_t modes_cap = 0;
     void *wbuf = nullptr;                  // W scratch of the tiled 4ph path
     size_t wbuf_bytes = 0;
+    int *perm4_dev = nullptr;              // device cluster slot -> input index (gradients)
+    double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
+    size_t adj_cap = 0;
+    double *adj_tmp = nullptr;             // Φ4 gradient in device cluster order
+    int *modes_last = nullptr;             // device copy of the last call's modes
     // last rates call
     bool have_last = false;
     double last_T = 300.0, last_sigma = 2.0 * kPi * 0.1;
@@ -394,6 +399,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
         FC4_TRY(upload(c, &c->phi4_32, ph32));
         FC4_TRY(upload(c, &d_ks, key_start));
         FC4_TRY(upload(c, &d_kr, kr));
+        FC4_TRY(upload(c, &c->perm4_dev, c->perm4));
+        FC4_TRY(dalloc(c, &c->adj_tmp, 81 * (size_t)std::max(1, c->nc4)));
         t.c4_at = d_at;
         t.c4_r3 = d_r3;
         t.c4_r13 = d_r13;
@@ -660,24 +667,91 @@ fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *
     return FC4_OK;
 }
 
-fc4_status fc4_kappa(fc4_ctx *c, double T_K, const double *gamma_total, double *kappa_out, void *stream) {
+// Σ C v v τ / (N V): v Å/ps -> m/s (1e2)², τ ps -> s (1e-12), V Å³ -> m³ (1e-30)
+static double kappa_scale(const fc4_ctx *c) { return 1e4 * 1e-12 / ((double)c->t.N * c->volume * 1e-30); }
+
+fc4_status fc4_kappa(fc4_ctx *c, double T_K, const double *gamma, int channel_mask, double *kappa_out,
+                     void *stream) {
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!(T_K > 0.0)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
-    if (!gamma_total || !kappa_out) return fail(c, FC4_ERR_INVALID, "NULL buffer");
-    // Σ C v v τ / (N V): v Å/ps -> m/s (1e2)², τ ps -> s (1e-12), V Å³ -> m³ (1e-30)
-    const double scale = 1e4 * 1e-12 / ((double)c->t.N * c->volume * 1e-30);
+    if (!gamma || !kappa_out) return fail(c, FC4_ERR_INVALID, "NULL buffer");
+    if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
     Timed tm(c, 6, (cudaStream_t)stream);
-    FC4_CUDA(c, fc4::launch_kappa(c->t, kHbar * 1e12 / (kKb * T_K), kKb, gamma_total, scale, kappa_out,
-                                  (cudaStream_t)stream));
+    FC4_CUDA(c, fc4::launch_kappa(c->t, kHbar * 1e12 / (kKb * T_K), kKb, gamma, channel_mask, kappa_scale(c),
+                                  kappa_out, (cudaStream_t)stream));
+    return FC4_OK;
+}
+
+fc4_status fc4_kappa_backward(fc4_ctx *c, double T_K, const double *gamma, int channel_mask,
+                              const double *dL_dkappa, double *dL_dgamma, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!(T_K > 0.0)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
+    if (!gamma || !dL_dkappa || !dL_dgamma) return fail(c, FC4_ERR_INVALID, "NULL buffer");
+    if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
+    FC4_CUDA(c, fc4::launch_kappa_backward(c->t, kHbar * 1e12 / (kKb * T_K), kKb, gamma, channel_mask,
+                                           kappa_scale(c), dL_dkappa, dL_dgamma, (cudaStream_t)stream));
+    c->n_launches += 1;
     return FC4_OK;
 }
 
 fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3, double *dphi4,
                               void *stream) {
-    (void)dL_dgamma; (void)dphi3; (void)dphi4; (void)stream;
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!c->have_last) return fail(c, FC4_ERR_STATE, "fc4_rates_backward before fc4_rates");
-    return fail(c, FC4_ERR_STATE, "fc4_rates_backward: adjoint kernels not available in this build");
+    if (c->t.n_atoms > 2) return fail(c, FC4_ERR_INVALID, "fc4_rates_backward supports cells of at most 2 atoms");
+    const int nm = (int)c->last_modes.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dphi3 && c->nc3) FC4_CUDA(c, cudaMemsetAsync(dphi3, 0, 27 * (size_t)c->nc3 * sizeof(double), s));
+    if (dphi4 && c->nc4) FC4_CUDA(c, cudaMemsetAsync(dphi4, 0, 81 * (size_t)c->nc4 * sizeof(double), s));
+    if (nm == 0) return FC4_OK;
+    if (!dL_dgamma) return fail(c, FC4_ERR_INVALID, "dL_dgamma is NULL");
+    const size_t width = std::max<size_t>(27 * (size_t)c->nc3, 81 * (size_t)c->nc4);
+    const size_t need = (size_t)nm * std::max<size_t>(width, 1);
+    if (need > c->adj_cap) {
+        if (c->adj_part) {
+            cudaFree(c->adj_part);
+            c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->adj_part));
+            c->adj_part = nullptr;
+            c->adj_cap = 0;
+        }
+        FC4_CUDA(c, dalloc(c, &c->adj_part, need));
+        c->adj_cap = need;
+    }
+    if ((size_t)nm > c->modes_cap) return fail(c, FC4_ERR_STATE, "mode buffer smaller than the last call");
+    FC4_CUDA(c, cudaMemcpyAsync(c->modes, c->last_modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+    fc4_status st = ensure_occupations(c, c->last_T, s);
+    if (st != FC4_OK) return st;
+    const double sigma = c->last_sigma;
+    fc4::RateArgs a{};
+    a.n_modes = nm;
+    a.modes = c->modes;
+    a.two_sigma = 2.0 * sigma;
+    a.inv_sigma2 = 1.0 / (sigma * sigma);
+    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    const double N = (double)c->t.N;
+    bool first3 = true, first4 = true;
+    for (int ch = 0; ch < 5; ++ch) {
+        if (!((c->last_mask >> ch) & 1)) continue;
+        if (ch < 2 && (!dphi3 || !c->nc3)) continue;
+        if (ch >= 2 && (!dphi4 || !c->nc4)) continue;
+        const double cst = ch < 2 ? unit_c3() / N : unit_c4() / (N * N);
+        FC4_CUDA(c, fc4::launch_adjoint(c->t, a, ch, dL_dgamma, cst, c->adj_part, s));
+        c->n_launches += 1;
+        if (ch < 2) {
+            FC4_CUDA(c, fc4::launch_sum_slices(nm, 27 * c->nc3, c->adj_part, dphi3, first3 ? 0 : 1, s));
+            first3 = false;
+        } else {
+            FC4_CUDA(c, fc4::launch_sum_slices(nm, 81 * c->nc4, c->adj_part, c->adj_tmp, first4 ? 0 : 1, s));
+            first4 = false;
+        }
+        c->n_launches += 1;
+    }
+    if (!first4) {
+        FC4_CUDA(c, fc4::launch_unpermute(c->nc4, 81, c->perm4_dev, c->adj_tmp, dphi4, s));
+        c->n_launches += 1;
+    }
+    return FC4_OK;
 }
 
 fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *phi4) {

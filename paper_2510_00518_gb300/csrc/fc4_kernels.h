@@ -92,7 +92,14 @@ cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ
 cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4, float2 *P4_32,
                                 cudaStream_t s);
 cudaError_t launch_kappa(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
-                         double scale, double *kappa, cudaStream_t s);
+                         int mask, double scale, double *kappa, cudaStream_t s);
+cudaError_t launch_kappa_backward(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
+                                  int mask, double scale, const double *dLdk, double *dLdg, cudaStream_t s);
+cudaError_t launch_unpermute(int nc, int width, const int *perm, const double *in, double *out, cudaStream_t s);
+cudaError_t launch_adjoint(const Tables &t, const RateArgs &a, int ch, const double *dLdG, double cst,
+                           double *part, cudaStream_t s);
+cudaError_t launch_sum_slices(int n_slices, int n, const double *part, double *out, int accumulate,
+                              cudaStream_t s);
 cudaError_t launch_count_processes(const Tables &t, int ch, int mode, double two_sigma,
                                    float lo32, float hi32, int *counts, cudaStream_t s);
 cudaError_t launch_write_processes(const Tables &t, int ch, int mode, double two_sigma,

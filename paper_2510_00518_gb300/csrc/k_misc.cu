@@ -304,16 +304,24 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
 
 // ------------------------------------------------------------------------------ kappa
 
+// Γ_tot(λ) = Σ over the channels in mask of gamma[ch][λ]
+__device__ __forceinline__ double gamma_total(const double *gamma, int nm, int mask, int i) {
+    double g = 0.0;
+    for (int ch = 0; ch < 5; ++ch)
+        if ((mask >> ch) & 1) g += gamma[(size_t)ch * nm + i];
+    return g;
+}
+
 // κ_ab = scale Σ_λ C_λ v_a v_b / Γ_λ, C = k_B x² n (n + 1), over modes with ω > 0 and Γ > 0.
 // One block; thread i sums modes i, i + 256, ... in order; fixed-order block sums.
 __global__ void __launch_bounds__(256)
 kappa_kernel(int nm, const double *om, const double *vel, double x_per_w, double kB,
-             const double *gamma, double scale, double *kappa) {
+             const double *gamma, int mask, double scale, double *kappa) {
     __shared__ double s_red[32];
     double acc[9];
     for (int k = 0; k < 9; ++k) acc[k] = 0.0;
     for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-        const double w = om[i], g = gamma[i];
+        const double w = om[i], g = gamma_total(gamma, nm, mask, i);
         if (!(w > 0.0) || !(g > 0.0)) continue;
         const double x = w * x_per_w;
         const double n = 1.0 / expm1(x);
@@ -329,8 +337,53 @@ kappa_kernel(int nm, const double *om, const double *vel, double x_per_w, double
 }
 
 cudaError_t launch_kappa(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
-                         double scale, double *kappa, cudaStream_t s) {
-    kappa_kernel<<<1, 256, 0, s>>>(t.N * t.nb, t.om, t.vel, hbar_over_kT, kB, gamma, scale, kappa);
+                         int mask, double scale, double *kappa, cudaStream_t s) {
+    kappa_kernel<<<1, 256, 0, s>>>(t.N * t.nb, t.om, t.vel, hbar_over_kT, kB, gamma, mask, scale, kappa);
+    return cudaGetLastError();
+}
+
+// dL/dΓ_ch(λ) = Σ_ab dL/dκ_ab dκ_ab/dΓ_tot(λ) = -scale C_λ (v . G v) / Γ_tot² for every channel in
+// mask (Γ_tot depends on each of them with weight 1); 0 for skipped modes and other channels.
+__global__ void kappa_backward_kernel(int nm, const double *om, const double *vel, double x_per_w, double kB,
+                                      const double *gamma, int mask, double scale, const double *dLdk,
+                                      double *dLdg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const double w = om[i], g = gamma_total(gamma, nm, mask, i);
+    double d = 0.0;
+    if (w > 0.0 && g > 0.0) {
+        const double x = w * x_per_w;
+        const double n = 1.0 / expm1(x);
+        const double c = kB * x * x * n * (n + 1.0);
+        const double *v = vel + 3 * (size_t)i;
+        double q = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) q += dLdk[3 * a + b] * v[a] * v[b];
+        d = -scale * c * q / (g * g);
+    }
+    for (int ch = 0; ch < 5; ++ch) dLdg[(size_t)ch * nm + i] = ((mask >> ch) & 1) ? d : 0.0;
+}
+
+cudaError_t launch_kappa_backward(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
+                                  int mask, double scale, const double *dLdk, double *dLdg, cudaStream_t s) {
+    const int nm = t.N * t.nb;
+    kappa_backward_kernel<<<(nm + 255) / 256, 256, 0, s>>>(nm, t.om, t.vel, hbar_over_kT, kB, gamma, mask,
+                                                            scale, dLdk, dLdg);
+    return cudaGetLastError();
+}
+
+// out[perm[s]][k] = in[s][k]: device cluster order back to the caller's order
+__global__ void unpermute_kernel(int nc, int width, const int *perm, const double *in, double *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nc * width) return;
+    const int s = (int)(i / width), k = (int)(i - (long long)s * width);
+    out[(size_t)perm[s] * width + k] = in[i];
+}
+
+cudaError_t launch_unpermute(int nc, int width, const int *perm, const double *in, double *out, cudaStream_t s) {
+    const long long n = (long long)nc * width;
+    if (n == 0) return cudaSuccess;
+    unpermute_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nc, width, perm, in, out);
     return cudaGetLastError();
 }
 

@@ -103,16 +103,15 @@ def test_rates_mixed_all_modes_3cubed(sys0, prob3, oracle3_all):
     assert np.array_equal(cnt.cpu().numpy(), CNT)
     assert_close(g.cpu().numpy(), G, 1e-4, floor_frac=1e-6, what="gamma mixed")
     # κ with 3ph + 4ph
-    gt = g.sum(0)
-    k_gpu = e.kappa(300.0, gt).cpu().numpy()
+    k_gpu = e.kappa(300.0, g, 31).cpu().numpy()
     k_ref = prob3.kappa(G.sum(0))
     assert np.abs(k_gpu - k_ref).max() <= 1e-4 * np.abs(k_ref).max()
 
 
 def test_kappa_fp64(eng3, prob3, oracle3_all):
     G = oracle3_all[0]
-    gt = torch.tensor(G.sum(0), device="cuda")
-    k = eng3.kappa(300.0, gt).cpu().numpy()
+    gt = torch.tensor(G, device="cuda")
+    k = eng3.kappa(300.0, gt, 31).cpu().numpy()
     kr = prob3.kappa(G.sum(0))
     assert np.abs(k - kr).max() <= 1e-10 * np.abs(kr).max()
 

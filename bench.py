@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--sigma", type=float, default=0.1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-mixed comparison")
+    p.add_argument("--batch", action="store_true",
+                   help="time the 24-crystal batch (6-24 branches) as one CUDA graph instead")
     p.add_argument("--cpu-qp", type=int, default=24, help="oracle sample: partners q' < cpu_qp")
     p.add_argument("--cpu-q", type=int, default=2, help="oracle sample: q points (x nb modes)")
     p.add_argument("--block-threads", type=int, default=0)
@@ -150,20 +153,58 @@ def clocks_stop(p, f, gpu_index):
 # ------------------------------------------------------------------------------ GPU arm
 
 def flops_alg(stats, info, nb):
-    """Algorithmic FP32 flops of the four-phonon kernel per channel (the factored contraction):
-    window 2 per candidate; W 9 * 46 per cluster per (λ, q', j'); Y 90 per key per item;
-    V 8 * nb + weight 24 per kept process (complex multiply-add = 8 flops)."""
-    nc4, nk = info["nc4"], info["n_keys"]
+    """Algorithmic FP32 flops of the four-phonon path per channel, counted for the factored
+    contraction it performs (complex multiply-add = 8 flops, real x complex = 4):
+      window          2 per candidate (add, subtract; the comparison is not counted)
+      W per (λ, q')   Φ~ = Σ_α Φ e_λ: nc4·27·3·4 / 8 (built once per 8 q'), plus
+                      W_r = Σ_c phase Σ_β e' Φ~: nc4·nb·9·(3 + 1)·8
+      X per entry     n_keys·9·8 (X[c,d] = Σ_r P_r W_r)
+      Y per item      nb²·8 (Y = X times the conjugated third-partner eigenvector)
+      per process     V nb·8, weight 30"""
+    nc4, nk, N = info["nc4"], info["n_keys"], info["N"]
     out = []
     for ch in range(5):
         if ch < 2:
             out.append(0.0)
             continue
-        cand = stats["candidates"][ch]
-        units_j = cand / (info["N"] * nb * nb)          # (λ, q', j') units
-        out.append(2.0 * cand + units_j * nc4 * 9 * 46 + stats["items"][ch] * nk * 90.0
-                   + stats["kept"][ch] * (8.0 * nb + 24.0))
+        cand = float(stats["candidates"][ch])
+        units = cand / (N * nb ** 3)                   # (λ, q') units
+        w = units * (nc4 * 27 * 3 * 4 / 8.0 + nc4 * nb * 9 * 4 * 8)
+        out.append(2.0 * cand + w + stats["entries"][ch] * nk * 72.0 + stats["items"][ch] * nb * nb * 8.0
+                   + stats["kept"][ch] * (8.0 * nb + 30.0))
     return out
+
+
+def fp64_comparison(args, sysm, mesh, g_mixed, local):
+    """FP64 GPU path beside the mixed one: throughput on a sampled q subset of the same workload,
+    the largest Γ relative error of the mixed path there, and the κ relative error mixed vs FP64
+    on the full 6x6x6 mesh of the same crystal."""
+    import torch
+    from paper_2510_00518_gb300 import Engine, FP64, MIXED
+    from synth.sampling import sample_q
+    qs = sample_q(int(np.prod(mesh)), 16, seed=0)
+    e64 = Engine(*sysm, mesh, precision=FP64)
+    e64.rates(args.T, args.sigma, 31, q_subset=qs)          # warm
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g64, _, _ = e64.rates(args.T, args.sigma, 31, q_subset=qs)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    kept = int(e64.stats()["kept"][2:].sum())
+    modes = torch.tensor([q * 6 + j for q in qs for j in range(6)], device=g64.device)
+    gm = g_mixed[:, modes]
+    floor = 1e-6 * g64.abs().amax(dim=1, keepdim=True)
+    gerr = float(((gm - g64).abs() / torch.maximum(g64.abs(), floor)).max())
+    ks = []
+    for prec in (MIXED, FP64):
+        e = Engine(*sysm, (6, 6, 6), precision=prec)
+        g6, _, _ = e.rates(args.T, args.sigma, 31)
+        ks.append(e.kappa(args.T, g6, 31).cpu().numpy())
+    kerr = float(np.abs(ks[0] - ks[1]).max() / np.abs(ks[1]).max())
+    return {"value": kept / (ms * 1e-3), "unit": UNIT, "ms": ms, "kept_4ph": kept,
+            "sample": f"16 q points (default_rng(0)) x 6 branches of the {mesh[0]}x{mesh[1]}x{mesh[2]} mesh, 5 channels",
+            "gamma_rel_err_max_mixed_vs_fp64": gerr, "kappa_rel_err_mixed_vs_fp64_6x6x6": kerr}
 
 
 def run_gpu(args):
@@ -261,6 +302,9 @@ def run_gpu(args):
               "kept_4ph_per_step": kept4, "candidates_4ph_per_step": int(stats["candidates"][2:].sum()),
               "wall_s": wall, "gpu_launches": int(launches), "roofline": roof, "clocks": clocks}
 
+    if not args.no_fp64 and world == 1:
+        result["fp64_gpu"] = fp64_comparison(args, sysm, mesh, g, local)
+
     # end to end through the C interface from host buffers
     if not args.no_e2e:
         import ctypes
@@ -328,6 +372,46 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """24 synthetic crystals (1x1xk diamond supercells, k = 1..4; 12³/10³/8³/6³ meshes; 4 seeded q
+    points each; mixed precision) evaluated as one CUDA graph; metric: kept 4ph processes/s."""
+    import torch
+    from paper_2510_00518_gb300 import Engine, MIXED
+    from paper_2510_00518_gb300.batch import BatchRunner, autotune
+    from synth import batch_crystal, morse_ifcs
+    from synth.sampling import sample_q
+    torch.cuda.set_device(0)
+    jobs = []
+    for seed in range(24):
+        c, mesh = batch_crystal(seed)
+        e = Engine(c, *morse_ifcs(c, seed=seed), mesh, precision=MIXED)
+        jobs.append((e, sample_q(int(np.prod(mesh)), 4, seed=seed)))
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    cache = os.path.join(out_dir, "tune_cache.json") if os.path.isdir(out_dir) else None
+    for e, qs in jobs:
+        if e.n_atoms > 2:
+            autotune(e, args.T, args.sigma, 31, qs, cache=cache)
+    runner = BatchRunner(jobs, args.T, args.sigma, 31)
+    kept = sum(int(e.stats()["kept"][2:].sum()) for e, _ in jobs)
+    for _ in range(args.warmup):
+        runner.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        runner.run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"metric": METRIC + " (batch of 24 crystals, one CUDA graph)", "value": kept / (ms * 1e-3),
+                      "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batch-24-morse-supercells-6to24-branches", "q_per_crystal": 4,
+                                 "meshes": "12^3/10^3/8^3/6^3 for 2/4/6/8 atoms", "graph": "one CUDA graph launch",
+                                 "l2": "not flushed (graph replays back to back)"},
+                      "kept_4ph_per_step": kept}))
+
+
 def run_once(args):
     """A single rates call on the workload (profiling helper, no timing, no JSON line)."""
     import torch
@@ -344,6 +428,8 @@ if __name__ == "__main__":
     a = parse()
     if a.once:
         run_once(a)
+    elif a.batch:
+        run_batch(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -116,7 +116,9 @@ fc4_status fc4_get_modes(fc4_ctx *ctx, double *omega, double *vel, double *evec)
  * q_subset: host array of n_q distinct q indices (NULL = all N q points, n_q ignored).
  * gamma_out, wp_out: device [5][n_q*nb] doubles; counts_out: device [5][n_q*nb] long long;
  * wp_out and counts_out may be NULL.  Channels outside channel_mask are written as 0.
- * The call records (T, σ, mask, subset) for fc4_rates_backward. */
+ * The call records (T, σ, mask, subset) for fc4_rates_backward.  After a first call with the same
+ * subset, size and T (which sizes every buffer), a call performs only stream-ordered kernel
+ * launches and memsets, so it can be captured in a CUDA graph (relaxed or thread-local mode). */
 fc4_status fc4_rates(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_value,
                      int channel_mask, const int *q_subset, int n_q, double *gamma_out,
                      double *wp_out, long long *counts_out, void *stream);
@@ -130,7 +132,7 @@ fc4_status fc4_rates(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_
  *
  * Same kernels, arithmetic and results as fc4_rates (fixed σ only, q_subset required, no stats).
  * Its per-call scratch (q list, mode list, per-(channel, mode, q') partials) is one file-scope
- * device array of 11 MB, created when the library is loaded and held by every GPU that loads it
+ * device array of 13 MB, created when the library is loaded and held by every GPU that loads it
  * until the process exits.  Limit: n_q * nb * N <= 65536 (e.g. all 27 q of a 3x3x3 mesh, or up
  * to 21 q of an 8x8x8 two-atom mesh); larger requests return FC4_ERR_INVALID and write nothing.
  * No cudaMalloc, cudaFree or other allocating routine is called.  The first call on a device
@@ -182,10 +184,11 @@ fc4_status fc4_rates_backward(fc4_ctx *ctx, const double *dL_dgamma, double *dph
  * as fc4_init; NULL keeps the current values).  Modes and phase tables are unchanged. */
 fc4_status fc4_update_anharmonic(fc4_ctx *ctx, const double *phi3, const double *phi4);
 
-/* fc4_stats - work counters of the last fc4_rates call (synchronises the device):
- * out[3*ch + 0] = kept processes, out[3*ch + 1] = four-phonon (q'', j''') items evaluated (0 for
- * 3ph), out[3*ch + 2] = candidate tuples before the window, for channels ch = 0..4. */
-fc4_status fc4_stats(fc4_ctx *ctx, long long out[15]);
+/* fc4_stats - work counters of the last fc4_rates call (synchronises the device), for channels
+ * ch = 0..4: out[4*ch + 0] kept processes, out[4*ch + 1] four-phonon (q'', j''') items
+ * evaluated, out[4*ch + 2] candidate tuples before the window, out[4*ch + 3] four-phonon
+ * (q'', j') entries whose cluster sum was contracted (items and entries are 0 for 3ph). */
+fc4_status fc4_stats(fc4_ctx *ctx, long long out[20]);
 
 /* fc4_timings - device time in ms of the kernels launched by the last fc4_rates / fc4_kappa
  * calls, measured with CUDA events recorded on the launching stream around each launch (needs
@@ -193,6 +196,10 @@ fc4_status fc4_stats(fc4_ctx *ctx, long long out[15]);
  * 0..4 (0 if not launched), out[5] the reduction, out[6] the conductivity, out[7] the occupation
  * table, out[8] the number of kernels libfc4 launched since the context was created. */
 fc4_status fc4_timings(fc4_ctx *ctx, double out[9]);
+
+/* fc4_set_block_threads - threads per block of the general four-phonon kernel (cells of more
+ * than 2 atoms): 64, 96 or 128 (0 = 128).  A tuning knob; results do not depend on it. */
+fc4_status fc4_set_block_threads(fc4_ctx *ctx, int block_threads);
 
 /* fc4_info - sizes of a context: out[0..7] = n_atoms, nb, N, nc2, nc3, nc4, n_keys, precision. */
 fc4_status fc4_info(const fc4_ctx *ctx, long long out[8]);

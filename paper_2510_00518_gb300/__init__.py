@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
         "fc4_stats": [vp, vp],
         "fc4_timings": [vp, vp],
         "fc4_rates_static": [vp, d, d, i, vp, i, vp, vp, vp, vp],
+        "fc4_set_block_threads": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -186,13 +187,18 @@ class Engine:
         keys = ("n_atoms", "nb", "N", "nc2", "nc3", "nc4", "n_keys", "precision")
         return dict(zip(keys, out.tolist()))
 
+    def set_block_threads(self, n: int):
+        """Tuning knob of the general four-phonon kernel (64, 96, 128; 0 = default)."""
+        self._check(self.lib.fc4_set_block_threads(self.ctx, int(n)))
+
     def stats(self) -> dict:
         """Work counters of the last rates call: kept processes, 4ph items and candidates per
         channel (synchronises the device)."""
-        out = np.zeros(15, np.int64)
+        out = np.zeros(20, np.int64)
         self._check(self.lib.fc4_stats(self.ctx, _ptr(out)))
-        o = out.reshape(5, 3)
-        return {"kept": o[:, 0].copy(), "items": o[:, 1].copy(), "candidates": o[:, 2].copy()}
+        o = out.reshape(5, 4)
+        return {"kept": o[:, 0].copy(), "items": o[:, 1].copy(), "candidates": o[:, 2].copy(),
+                "entries": o[:, 3].copy()}
 
     def timings(self) -> dict:
         """Per-kernel device times (ms) of the last rates / kappa calls and the launch count."""

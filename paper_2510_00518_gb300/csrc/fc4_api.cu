@@ -64,9 +64,9 @@ struct fc4_ctx {
     double occ_T = -1.0;
     // scratch
     double *part_g = nullptr, *part_wp = nullptr;
-    long long *part_n = nullptr, *part_items = nullptr;
+    long long *part_n = nullptr, *part_items = nullptr, *part_ent = nullptr;
     size_t part_cap = 0;
-    unsigned long long *stats = nullptr;    // [10] kept and items per channel of the last call
+    unsigned long long *stats = nullptr;    // [15] kept, items, entries per channel of the last call
     long long cand[5] = {0, 0, 0, 0, 0};    // candidates per channel of the last call
     int *modes = nullptr;
     size_t modes_cap = 0;
@@ -76,7 +76,7 @@ struct fc4_ctx {
     double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
     size_t adj_cap = 0;
     double *adj_tmp = nullptr;             // Φ4 gradient in device cluster order
-    int *modes_last = nullptr;             // device copy of the last call's modes
+    std::vector<int> modes_on_device;      // content of `modes` (skip re-uploading an unchanged list)
     // last rates call
     bool have_last = false;
     double last_T = 300.0, last_sigma = 2.0 * kPi * 0.1;
@@ -531,21 +531,27 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         if (c->modes) { cudaFree(c->modes); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->modes)); }
         FC4_CUDA(c, dalloc(c, &c->modes, (size_t)nm));
         c->modes_cap = nm;
+        c->modes_on_device.clear();
     }
     const size_t need = (size_t)5 * nm * N;
     if (need > c->part_cap) {
-        for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items})
+        for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items,
+                        (void *)c->part_ent})
             if (p) { cudaFree(p); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), p)); }
         c->part_g = c->part_wp = nullptr;
-        c->part_n = c->part_items = nullptr;
+        c->part_n = c->part_items = c->part_ent = nullptr;
         c->part_cap = 0;
         FC4_CUDA(c, dalloc(c, &c->part_g, need));
         FC4_CUDA(c, dalloc(c, &c->part_wp, need));
         FC4_CUDA(c, dalloc(c, &c->part_n, need));
         FC4_CUDA(c, dalloc(c, &c->part_items, need));
+        FC4_CUDA(c, dalloc(c, &c->part_ent, need));
         c->part_cap = need;
     }
-    FC4_CUDA(c, cudaMemcpyAsync(c->modes, modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (modes != c->modes_on_device) {      // unchanged subsets need no copy (stream capture)
+        FC4_CUDA(c, cudaMemcpyAsync(c->modes, modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+        c->modes_on_device = modes;
+    }
     fc4_status st = ensure_occupations(c, T_K, s);
     if (st != FC4_OK) return st;
     const double sigma = 2.0 * kPi * sigma_value;
@@ -555,11 +561,14 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     a.two_sigma = 2.0 * sigma;
     a.inv_sigma2 = 1.0 / (sigma * sigma);
     a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    a.inv_sigma2_32 = (float)a.inv_sigma2;
+    a.gnorm32 = (float)a.gnorm;
     prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
     a.part_g = c->part_g;
     a.part_wp = c->part_wp;
     a.part_n = c->part_n;
     a.part_items = c->part_items;
+    a.part_ent = c->part_ent;
     {   // W scratch of the tiled 4ph path: up to 4 GiB, in whole modes, grown on demand
         const size_t per_mode = fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64);
         if (per_mode && (channel_mask & 0b11100) && c->nc4) {
@@ -581,8 +590,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         a.wbuf = c->wbuf;
         a.wbuf_bytes = c->wbuf_bytes;
     }
-    if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 10));
-    FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 10 * sizeof(unsigned long long), s));
+    if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 15));
+    FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 15 * sizeof(unsigned long long), s));
     const int fp64 = c->precision == FC4_FP64;
     for (int ch = 0; ch < 5; ++ch) {
         if (!((channel_mask >> ch) & 1)) continue;
@@ -718,7 +727,10 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
         c->adj_cap = need;
     }
     if ((size_t)nm > c->modes_cap) return fail(c, FC4_ERR_STATE, "mode buffer smaller than the last call");
-    FC4_CUDA(c, cudaMemcpyAsync(c->modes, c->last_modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (c->last_modes != c->modes_on_device) {
+        FC4_CUDA(c, cudaMemcpyAsync(c->modes, c->last_modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+        c->modes_on_device = c->last_modes;
+    }
     fc4_status st = ensure_occupations(c, c->last_T, s);
     if (st != FC4_OK) return st;
     const double sigma = c->last_sigma;
@@ -728,6 +740,8 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
     a.two_sigma = 2.0 * sigma;
     a.inv_sigma2 = 1.0 / (sigma * sigma);
     a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    a.inv_sigma2_32 = (float)a.inv_sigma2;
+    a.gnorm32 = (float)a.gnorm;
     prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
     const double N = (double)c->t.N;
     bool first3 = true, first4 = true;
@@ -773,16 +787,17 @@ fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *p
     return FC4_OK;
 }
 
-fc4_status fc4_stats(fc4_ctx *c, long long out[15]) {
+fc4_status fc4_stats(fc4_ctx *c, long long out[20]) {
     if (!c || !out) return fail(c, FC4_ERR_INVALID, "NULL argument");
     if (!c->have_last || !c->stats) return fail(c, FC4_ERR_STATE, "fc4_stats before fc4_rates");
-    unsigned long long h[10];
+    unsigned long long h[15];
     FC4_CUDA(c, cudaDeviceSynchronize());
     FC4_CUDA(c, cudaMemcpy(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int ch = 0; ch < 5; ++ch) {
-        out[3 * ch] = (long long)h[2 * ch];
-        out[3 * ch + 1] = (long long)h[2 * ch + 1];
-        out[3 * ch + 2] = c->cand[ch];
+        out[4 * ch] = (long long)h[3 * ch];
+        out[4 * ch + 1] = (long long)h[3 * ch + 1];
+        out[4 * ch + 2] = c->cand[ch];
+        out[4 * ch + 3] = (long long)h[3 * ch + 2];
     }
     return FC4_OK;
 }
@@ -799,6 +814,14 @@ fc4_status fc4_timings(fc4_ctx *c, double out[9]) {
         out[k] = ms;
     }
     out[8] = (double)c->n_launches;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_block_threads(fc4_ctx *c, int block_threads) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (block_threads != 0 && block_threads != 64 && block_threads != 96 && block_threads != 128)
+        return fail(c, FC4_ERR_INVALID, "block_threads must be 0, 64, 96 or 128");
+    c->block_threads = block_threads ? block_threads : 128;
     return FC4_OK;
 }
 
@@ -844,7 +867,7 @@ namespace {
 constexpr long long kStaticUnits = 1LL << 16;       // max (modes x q') units per channel
 constexpr long long kStaticQ = kStaticUnits;         // max q points (n_q <= units)
 constexpr size_t kStaticBytes =
-    5 * (size_t)kStaticUnits * (2 * sizeof(double) + 2 * sizeof(long long)) +
+    5 * (size_t)kStaticUnits * (2 * sizeof(double) + 3 * sizeof(long long)) +
     2 * (size_t)kStaticQ * sizeof(int);
 
 static __device__ __align__(256) unsigned char g_fc4_static_scratch[kStaticBytes];
@@ -901,7 +924,8 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
     double *part_wp = part_g + 5 * units;
     long long *part_n = reinterpret_cast<long long *>(part_wp + 5 * units);
     long long *part_items = part_n + 5 * units;
-    int *d_q = reinterpret_cast<int *>(part_items + 5 * units);
+    long long *part_ent = part_items + 5 * units;
+    int *d_q = reinterpret_cast<int *>(part_ent + 5 * units);
     int *d_modes = d_q + kStaticQ;
     FC4_CUDA(c, cudaMemcpyAsync(d_q, q_subset, (size_t)n_q * sizeof(int), cudaMemcpyHostToDevice, s));
     expand_modes_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(d_q, n_q, nb, d_modes);
@@ -915,11 +939,14 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
     a.two_sigma = 2.0 * sigma;
     a.inv_sigma2 = 1.0 / (sigma * sigma);
     a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+    a.inv_sigma2_32 = (float)a.inv_sigma2;
+    a.gnorm32 = (float)a.gnorm;
     prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
     a.part_g = part_g;
     a.part_wp = part_wp;
     a.part_n = part_n;
     a.part_items = part_items;
+    a.part_ent = part_ent;
     const int fp64 = c->precision == FC4_FP64;
     const size_t chunk = (size_t)nm * N;
     for (int ch = 0; ch < 5; ++ch) {
@@ -930,6 +957,7 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
             FC4_CUDA(c, cudaMemsetAsync(part_wp + ch * chunk, 0, chunk * sizeof(double), s));
             FC4_CUDA(c, cudaMemsetAsync(part_n + ch * chunk, 0, chunk * sizeof(long long), s));
             FC4_CUDA(c, cudaMemsetAsync(part_items + ch * chunk, 0, chunk * sizeof(long long), s));
+            FC4_CUDA(c, cudaMemsetAsync(part_ent + ch * chunk, 0, chunk * sizeof(long long), s));
             continue;
         }
         if (ch < 2) FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));

@@ -61,10 +61,12 @@ struct RateArgs {
     double inv_sigma2;           // 1/σ²
     double gnorm;                // 1/(σ sqrt(π))
     float lo32, hi32;            // prefilter: |Δ32| <= lo keep, > hi reject, else exact
+    float inv_sigma2_32, gnorm32;  // FP32 copies of 1/σ² and 1/(σ sqrt(π)) (mixed weights)
     double *part_g;              // [5][n_modes][N] per-(mode, q') partial sums
     double *part_wp;
     long long *part_n;           // kept processes
     long long *part_items;       // 4ph: (q'', j''') items evaluated; 3ph: 0
+    long long *part_ent;         // 4ph: (q'', j') entries whose X or Y was contracted; 3ph: 0
     int n_part[5];               // partial slots written per mode for each channel (<= N)
     void *wbuf;                  // optional scratch for the tiled 4ph path (W per (λ, q')); may be NULL
     size_t wbuf_bytes;

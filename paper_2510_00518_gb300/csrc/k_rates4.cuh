@@ -168,7 +168,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const R *invw = Sel<R>::invw(t);
 
     Acc<R> acc_g, acc_wp;
-    long long acc_n = 0, acc_items = 0;
+    long long acc_n = 0, acc_items = 0, acc_ent = 0;
 
     const bool active = !(q0 == 0 && j0 < 3);
     if (active) {
@@ -256,6 +256,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                 __syncthreads();
 
                 for (int it = threadIdx.x; it < total; it += blockDim.x) {
+                    ++acc_ent;
                     const unsigned long long e = sQ[it];
                     const int iq2 = XROUTE ? (int)(e >> 40) : (int)e;
                     const int4 c2 = t.qc[iq2];
@@ -374,12 +375,14 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const double wp = block_sum(acc_wp.value(), s_red);
     const long long n = block_sum(acc_n, s_redn);
     const long long ni = block_sum(acc_items, s_redn);
+    const long long ne = block_sum(acc_ent, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
         a.part_g[o] = g;
         a.part_wp[o] = wp;
         a.part_n[o] = n;
         a.part_items[o] = ni;
+        a.part_ent[o] = ne;
     }
 }
 

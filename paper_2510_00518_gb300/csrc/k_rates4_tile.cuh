@@ -119,7 +119,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     const R *invw = Sel<R>::invw(t);
 
     Acc<R> acc_g, acc_wp;
-    long long acc_n = 0, acc_items = 0;
+    long long acc_n = 0, acc_items = 0, acc_ent = 0;
     const unsigned vm1 = t.vmask[q1];
 
     if (!(q0 == 0 && j0 < 3) && vm1) {
@@ -184,12 +184,22 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
             __syncthreads();
 
             for (int it = threadIdx.x; it < total; it += kTileQ) {
+                ++acc_ent;
                 const unsigned long long e = sQ[it];
                 const int iq2 = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
                 const int4 cc2 = t.qc[iq2];
                 const int iq3 = q_index(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
                                         t.mesh[0], t.mesh[1], t.mesh[2]);
                 const int m1 = q1 * NB + j1;
+                // per-entry constants of the mixed weight: TwoSum of ω + s1 ω', the sum of their lo
+                // parts, n', 1/(ω ω')
+                float ex1 = 0.0f, ee1 = 0.0f, el01 = 0.0f, iw01 = 0.0f, n1f = 0.0f;
+                if constexpr (sizeof(R) == 4) {
+                    ex1 = two_sum(t.om32[m0], (float)s1 * t.om32[m1], ee1);
+                    el01 = t.om32lo[m0] + (float)s1 * t.om32lo[m1];
+                    iw01 = invw[m0] * invw[m1];
+                    n1f = occ[m1];
+                }
                 const C *Prow = P4 + (size_t)iq2 * nk;
                 const C *Wj = sW + j1 * nk * 9;
                 C X[XROUTE ? NA : 1][XROUTE ? NA : 1][9];
@@ -251,6 +261,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     }
                     const int m3 = iq3 * NB + j3;
                     const R n3 = occ[m3], iw3 = invw[m3];
+                    float h3 = 0.0f, l3 = 0.0f;
+                    if constexpr (sizeof(R) == 4) {
+                        h3 = t.om32[m3];
+                        l3 = t.om32lo[m3];
+                    }
                     while (m) {
                         const int j2 = __ffs(m) - 1;
                         m &= m - 1;
@@ -268,11 +283,15 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
                                 g * invw[m0] * invw[m1] * invw[m2] * iw3;
                         } else {
-                            const float df = delta_comp(t.om32[m0], t.om32lo[m0], t.om32[m1], t.om32lo[m1],
-                                                        t.om32[m2], t.om32lo[m2], t.om32[m3], t.om32lo[m3], s1, s2);
-                            const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
-                            w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
-                                (invw[m0] * invw[m1]) * (invw[m2] * iw3);
+                            // Δ from the entry's TwoSum (ex1, ee1) and the hi/lo splits of the last two ω
+                            float e2s, e3s;
+                            const float x2 = two_sum(ex1, (float)s2 * t.om32[m2], e2s);
+                            const float x3 = two_sum(x2, -h3, e3s);
+                            const float lo = (el01 + (float)s2 * t.om32lo[m2]) - l3;
+                            const float df = x3 + ((ee1 + e2s) + (e3s + lo));
+                            const float gs = __expf(-(df * df) * a.inv_sigma2_32) * a.gnorm32;
+                            w = sym4<float>(ch) * occupation_factor<float>(ch, n1f, occ[m2], n3) * gs *
+                                iw01 * (invw[m2] * iw3);
                         }
                         acc_wp.add(w);
                         acc_g.add(w * (V.x * V.x + V.y * V.y));
@@ -287,12 +306,14 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     const double wp = block_sum(acc_wp.value(), s_red);
     const long long n = block_sum(acc_n, s_redn);
     const long long ni = block_sum(acc_items, s_redn);
+    const long long ne = block_sum(acc_ent, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
         a.part_g[o] = g;
         a.part_wp[o] = wp;
         a.part_n[o] = n;
         a.part_items[o] = ni;
+        a.part_ent[o] = ne;
     }
 }
 

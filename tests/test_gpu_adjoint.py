@@ -87,6 +87,6 @@ def test_kappa_gradient_autograd_vs_finite_differences(sysm):
                 vals.append(float(kxx(a3, a4)))
         fd = (vals[0] - vals[1]) / (2 * h)
         an = float((p3.grad if order == 3 else p4.grad)[c, x])
-        noise = 1e-15 * abs(float(k)) / h            # rounding of κ, amplified by the difference
+        noise = 1e-15 * abs(float(k.detach())) / h            # rounding of κ, amplified by the difference
         assert abs(fd - an) <= 1e-6 * abs(an) + noise, (order, c, x, fd, an, noise)
     e.update_anharmonic(sysm[2].phi, sysm[3].phi)

@@ -198,3 +198,13 @@ def test_config_8cubed_sampled_modes(sys0):
         G, WP, CNT = prob.rates(ms)
         assert np.array_equal(cnt[:, ms], CNT)
         assert_close(g[:, ms], G, tol, floor_frac=1e-6, what="8^3")
+
+
+def test_sharded_rates_kappa_single_process(eng3, oracle3_all, prob3):
+    """The sharding helper on one process (no process group): its q block is the whole mesh and
+    κ equals the oracle's."""
+    from paper_2510_00518_gb300.dist import sharded_rates_kappa
+    qs, g, k = sharded_rates_kappa(eng3, 300.0, 0.1, 31)
+    assert np.array_equal(qs, np.arange(27))
+    kr = prob3.kappa(oracle3_all[0].sum(0))
+    assert np.abs(k.cpu().numpy() - kr).max() <= 1e-10 * np.abs(kr).max()

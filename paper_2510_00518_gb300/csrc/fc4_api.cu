@@ -72,6 +72,8 @@ struct fc4_ctx {
     size_t modes_cap = 0;
     void *wbuf = nullptr;                  // W scratch of the tiled 4ph path
     size_t wbuf_bytes = 0;
+    int w_s1 = 0;                          // sign s1 of the W held for w_modes (0: none)
+    std::vector<int> w_modes;
     int *perm4_dev = nullptr;              // device cluster slot -> input index (gradients)
     double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
     size_t adj_cap = 0;
@@ -482,6 +484,7 @@ fc4_status fc4_set_modes(fc4_ctx *c, const double *omega, const double *vel, con
     FC4_CUDA(c, cudaMemcpy(c->om, omega, nm * sizeof(double), cudaMemcpyHostToDevice));
     FC4_CUDA(c, cudaMemcpy(c->vel, vel, 3 * nm * sizeof(double), cudaMemcpyHostToDevice));
     FC4_CUDA(c, cudaMemcpy(c->ev, evec, nm * c->t.nb * sizeof(double2), cudaMemcpyHostToDevice));
+    c->w_s1 = 0;
     fc4_status s = refresh_modes(c);
     if (s != FC4_OK) return s;
     FC4_CUDA(c, cudaDeviceSynchronize());
@@ -569,10 +572,17 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     a.part_n = c->part_n;
     a.part_items = c->part_items;
     a.part_ent = c->part_ent;
-    {   // W scratch of the tiled 4ph path: up to 4 GiB, in whole modes, grown on demand
+    size_t w_per_mode = 0;
+    {   // W scratch of the tiled 4ph path, in whole modes, grown on demand: up to a quarter of the
+        // device memory (at least 4 GiB), so that typical mode sets fit in one chunk and the ++ and
+        // +- channels share one W
         const size_t per_mode = fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64);
+        w_per_mode = per_mode;
         if (per_mode && (channel_mask & 0b11100) && c->nc4) {
-            const size_t cap_modes = std::max<size_t>(1, std::min<size_t>((size_t)nm, (4ull << 30) / per_mode));
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+            const size_t cap_bytes = std::max<size_t>(4ull << 30, total_b / 4);
+            const size_t cap_modes = std::max<size_t>(1, std::min<size_t>((size_t)nm, cap_bytes / per_mode));
             const size_t want = cap_modes * per_mode;
             if (c->wbuf_bytes < want) {
                 if (c->wbuf) {
@@ -585,6 +595,7 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
                 FC4_CUDA(c, dalloc(c, &w, want));
                 c->wbuf = w;
                 c->wbuf_bytes = want;
+                c->w_s1 = 0;
             }
         }
         a.wbuf = c->wbuf;
@@ -613,8 +624,17 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
                 FC4_CUDA(c, cudaMemsetAsync(c->part_items + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
                 continue;
             }
+            const int s1 = ch == 4 ? -1 : 1;
+            const bool whole = w_per_mode && c->wbuf && (size_t)nm * w_per_mode <= c->wbuf_bytes;
+            a.w_reuse = whole && c->w_s1 == s1 && c->w_modes == modes;
             Timed tm(c, ch, s);
             FC4_CUDA(c, fc4::launch_rates4(c->t, a, ch, fp64, c->block_threads, s));
+            if (whole && a.wbuf) {
+                c->w_s1 = s1;
+                if (c->w_modes != modes) c->w_modes = modes;
+            } else {
+                c->w_s1 = 0;
+            }
         }
     }
     for (int k = 0; k < 5; ++k)
@@ -771,6 +791,7 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
 fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *phi4) {
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     FC4_CUDA(c, cudaDeviceSynchronize());
+    if (phi4) c->w_s1 = 0;
     if (phi3 && c->nc3)
         FC4_CUDA(c, cudaMemcpy(c->phi3, phi3, 27 * (size_t)c->nc3 * sizeof(double), cudaMemcpyHostToDevice));
     if (phi4 && c->nc4) {

@@ -58,6 +58,19 @@ __device__ __forceinline__ int q_index(int c0, int c1, int c2, int n0, int n1, i
     return mod_pos(c0, n0) + n0 * (mod_pos(c1, n1) + n1 * mod_pos(c2, n2));
 }
 
+// x mod n for x in [-2n, 3n) (sums of up to three mesh coordinates with signs): no division
+__device__ __forceinline__ int mod_near(int x, int n) {
+    x = x < 0 ? x + n : x;
+    x = x < 0 ? x + n : x;
+    x = x >= n ? x - n : x;
+    x = x >= n ? x - n : x;
+    return x;
+}
+
+__device__ __forceinline__ int q_index_near(int c0, int c1, int c2, int n0, int n1, int n2) {
+    return mod_near(c0, n0) + n0 * (mod_near(c1, n1) + n1 * mod_near(c2, n2));
+}
+
 // phase index of exp(i q.R) = exp(2πi k / L): k = Σ_a q_a R_a (L / n_a) mod L, where rl holds
 // the precomputed R_a (L / n_a) reduced modulo L
 __device__ __forceinline__ int phase_index(int4 q, int4 rl, int L) {
@@ -141,6 +154,42 @@ __device__ __forceinline__ T block_sum(T v, T *s_red) {
         for (int w = 0; w < nw; ++w) r += s_red[w];
     __syncthreads();
     return r;
+}
+
+// Several deterministic block sums in one pass (two barriers); results valid in thread 0.
+// s_d must hold 32 * ND doubles, s_n 32 * NL long longs.
+template <int ND, int NL>
+__device__ __forceinline__ void block_sum_multi(double (&d)[ND], long long (&n)[NL], double *s_d, long long *s_n) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < ND; ++k) d[k] += __shfl_xor_sync(kFull, d[k], o);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) n[k] += __shfl_xor_sync(kFull, n[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; ++k) s_d[32 * k + wid] = d[k];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) s_n[32 * k + wid] = n[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+            double r = 0.0;
+            for (int w = 0; w < nw; ++w) r += s_d[32 * k + w];
+            d[k] = r;
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            long long r = 0;
+            for (int w = 0; w < nw; ++w) r += s_n[32 * k + w];
+            n[k] = r;
+        }
+    }
+    __syncthreads();
 }
 
 }  // namespace fc4

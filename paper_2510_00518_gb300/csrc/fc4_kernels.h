@@ -70,6 +70,7 @@ struct RateArgs {
     int n_part[5];               // partial slots written per mode for each channel (<= N)
     void *wbuf;                  // optional scratch for the tiled 4ph path (W per (λ, q')); may be NULL
     size_t wbuf_bytes;
+    int w_reuse;                 // 1: wbuf already holds W of every mode for this channel's sign s1
 };
 
 // launchers (stream-ordered; return cudaGetLastError())

@@ -15,6 +15,7 @@
 namespace fc4 {
 
 constexpr int kTileQ = 128;
+constexpr int kQPT = 4;            // partner points q'' per thread and compaction round
 
 __host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; }
 
@@ -103,10 +104,10 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
 
     extern __shared__ __align__(16) unsigned char smem[];
     C *sW = reinterpret_cast<C *>(smem);                        // [NB][nk][9]
-    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB]
+    unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB * kQPT]
     __shared__ int s_scan[32];
-    __shared__ double s_red[32];
-    __shared__ long long s_redn[32];
+    __shared__ double s_red[2 * 32];
+    __shared__ long long s_redn[3 * 32];
 
     const int unit = blockIdx.x;                                // (mode - mode0) * N + q'
     const int ml = unit / N, q1 = unit - ml * N;
@@ -135,15 +136,14 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
 #pragma unroll
         for (int j = 0; j < NB; ++j) base32[j] = w0f + (float)s1 * t.om32[q1 * NB + j];
 
-        for (int qb = 0; qb < N; qb += kTileQ) {
-            const int q2 = qb + threadIdx.x;
-            // window: this thread's q'' against every partner branch j'
+        for (int qb = 0; qb < N; qb += kTileQ * kQPT) {
+            // window: this thread's q'' of the round (up to kQPT) against every partner branch j'
             int n_ent = 0;
-            unsigned long long ent[NB];
-            if (q2 < N) {
+            unsigned long long ent[NB * kQPT];
+            for (int q2 = qb + threadIdx.x; q2 < min(N, qb + kTileQ * kQPT); q2 += kTileQ) {
                 const int4 c2 = t.qc[q2];
-                const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
-                                       t.mesh[0], t.mesh[1], t.mesh[2]);
+                const int q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                 const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
                 float w2f[NB], w3f[NB];
 #pragma unroll
@@ -174,7 +174,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             sure |= 1ull << k;
                     }
                     if (sure)
-                        ent[n_ent++] = ((unsigned long long)threadIdx.x << 48) |
+                        ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
                                        ((unsigned long long)j1 << 40) | sure;
                 }
             }
@@ -188,8 +188,8 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 const unsigned long long e = sQ[it];
                 const int iq2 = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
                 const int4 cc2 = t.qc[iq2];
-                const int iq3 = q_index(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
-                                        t.mesh[0], t.mesh[1], t.mesh[2]);
+                const int iq3 = q_index_near(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
+                                             t.mesh[0], t.mesh[1], t.mesh[2]);
                 const int m1 = q1 * NB + j1;
                 // per-entry constants of the mixed weight: TwoSum of ω + s1 ω', the sum of their lo
                 // parts, n', 1/(ω ω')
@@ -302,18 +302,16 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
             __syncthreads();                                     // sQ reused by the next round
         }
     }
-    const double g = block_sum(acc_g.value(), s_red);
-    const double wp = block_sum(acc_wp.value(), s_red);
-    const long long n = block_sum(acc_n, s_redn);
-    const long long ni = block_sum(acc_items, s_redn);
-    const long long ne = block_sum(acc_ent, s_redn);
+    double sums[2] = {acc_g.value(), acc_wp.value()};
+    long long cnts[3] = {acc_n, acc_items, acc_ent};
+    block_sum_multi<2, 3>(sums, cnts, s_red, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
-        a.part_g[o] = g;
-        a.part_wp[o] = wp;
-        a.part_n[o] = n;
-        a.part_items[o] = ni;
-        a.part_ent[o] = ne;
+        a.part_g[o] = sums[0];
+        a.part_wp[o] = sums[1];
+        a.part_n[o] = cnts[0];
+        a.part_items[o] = cnts[1];
+        a.part_ent[o] = cnts[2];
     }
 }
 
@@ -321,7 +319,7 @@ template <typename R, int NA>
 size_t tile_smem_bytes(const Tables &t) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
-    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB;
+    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB * kQPT;
     return (b + 15) & ~size_t(15);
 }
 
@@ -349,10 +347,12 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
     for (int m = 0; m < a.n_modes; m += chunk) {
         const int nm = min(chunk, a.n_modes - m);
         const long long ngrp = (t.N + kW4Group - 1) / kW4Group;
-        w4_kernel<R, NA><<<(unsigned)((long long)nm * ngrp), 128, wsmem, s>>>(t, a, ch, m,
-                                                                              reinterpret_cast<C *>(a.wbuf));
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if (!(a.w_reuse && nm == a.n_modes)) {           // W of the previous channel with the same s1
+            w4_kernel<R, NA><<<(unsigned)((long long)nm * ngrp), 128, wsmem, s>>>(t, a, ch, m,
+                                                                                  reinterpret_cast<C *>(a.wbuf));
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         rates4_tile_kernel<R, NA><<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(
             t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
         e = cudaGetLastError();

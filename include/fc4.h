@@ -112,7 +112,13 @@ fc4_status fc4_get_modes(fc4_ctx *ctx, double *omega, double *vel, double *evec)
  *   (e^+ = e, e^- = conj(e); C3 = ħπ/4, C4 = ħ²π/8 converted to ps^-1.)
  *
  * T_K > 0.  sigma_adaptive = 0: fixed Gaussian width sigma_value in THz (σ = 2π sigma_value
- * rad/ps).  Adaptive widths are not supported by this entry point (FC4_ERR_INVALID).
+ * rad/ps).  sigma_adaptive = 1: adaptive width per process from the group velocities of the two
+ * legs that the free partner sum moves together (3ph: λ', λ''; 4ph: λ'', λ'''),
+ *   σ = s sqrt(Σ_k ((Δv . b_k) / n_k)² / 6),  s = sigma_value (the scale factor, > 0),
+ * b_k the reciprocal vectors and n_k the mesh; a process is kept iff σ > 1e-9 rad/ps and
+ * |Δ| <= 2σ, both in FP64 (legs of equal velocity, or velocities equal by symmetry up to rounding
+ * noise, give no usable width and the process is dropped).  Any other sigma_adaptive value,
+ * or sigma_value <= 0 or not finite, returns FC4_ERR_INVALID.
  * q_subset: host array of n_q distinct q indices (NULL = all N q points, n_q ignored).
  * gamma_out, wp_out: device [5][n_q*nb] doubles; counts_out: device [5][n_q*nb] long long;
  * wp_out and counts_out may be NULL.  Channels outside channel_mask are written as 0.
@@ -151,7 +157,7 @@ fc4_status fc4_rates_static(fc4_ctx *ctx, double T_K, double sigma_value, int ch
  *   4ph: word = (((q' nb + j') N + q'') nb + j'') nb + j'''
  * words: host array of capacity cap (may be NULL when cap = 0); *n_out receives the count even
  * when it exceeds cap (then only the first cap words are written).  Uses the (T, σ) of the last
- * fc4_rates call, or 300 K and 0.1 THz before any. */
+ * fc4_rates call (fixed or adaptive), or 300 K and a fixed 0.1 THz before any. */
 fc4_status fc4_processes(fc4_ctx *ctx, int channel, int mode, unsigned long long *words,
                          long long cap, long long *n_out);
 
@@ -170,8 +176,9 @@ fc4_status fc4_kappa_backward(fc4_ctx *ctx, double T_K, const double *gamma, int
                               const double *dL_dkappa, double *dL_dgamma, void *stream);
 
 /* fc4_rates_backward - gradient of L = Σ_{ch,i} dL_dgamma[ch][i] Γ_ch(i) with respect to every
- * stored Φ3 and Φ4 entry (entries independent), at fixed modes and σ, for the (T, σ, mask,
- * subset) of the last fc4_rates call, in FP64 whatever the context's precision:
+ * stored Φ3 and Φ4 entry (entries independent), at fixed modes and σ (fixed or adaptive: both
+ * depend on the modes only), for the (T, σ, mask, subset) of the last fc4_rates call, in FP64
+ * whatever the context's precision:
  *   dL/dΦ_c = Σ_processes dL/dΓ C/N^k w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
  * Deterministic (fixed summation order).  dL_dgamma: device [5][n_q*nb]; dphi3: device
  * [nc3][27]; dphi4: device [nc4][81], in the cluster order given to fc4_init (overwritten;

@@ -65,8 +65,17 @@ C3, C4 = unit_constants_si()
 # ----------------------------------------------------------------------------- mesh
 
 def reciprocal(lattice: np.ndarray) -> np.ndarray:
-    """Rows b_i with a_i . b_j = 2π δ_ij."""
-    return 2.0 * math.pi * np.linalg.inv(lattice).T
+    """Rows b_i with a_i . b_j = 2π δ_ij, by the cross-product formula
+    b_1 = 2π (a_2 x a_3) / (a_1 . (a_2 x a_3)) (cyclic), evaluated left to right in IEEE double."""
+    a = [[float(x) for x in row] for row in np.asarray(lattice, dtype=np.float64)]
+
+    def cross(u, v):
+        return [u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]]
+
+    c = [cross(a[1], a[2]), cross(a[2], a[0]), cross(a[0], a[1])]
+    vol = a[0][0] * c[0][0] + a[0][1] * c[0][1] + a[0][2] * c[0][2]
+    f = 2.0 * math.pi / vol
+    return np.array([[f * c[i][x] for x in range(3)] for i in range(3)])
 
 
 def q_coords(mesh) -> np.ndarray:

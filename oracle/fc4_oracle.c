@@ -32,6 +32,10 @@
  *     4ph --: F = (1+n')(1+n'')(1+n''') - n'n''n''' sym = 1/6
  *   Γ3 = C3 / N  Σ w |V3|²,  Γ4 = C4 / N² Σ w |V4|²;  WP3 = Σ w / N,  WP4 = Σ w / N².
  *
+ * Broadening: fixed σ, or adaptive σ = s sqrt(Σ_k ((Δv . b_k) / n_k)² / 6) from the velocity
+ * difference of the two legs the free partner sum moves together (3ph: v' - v''; 4ph: v'' - v''');
+ * with adaptive widths a process is kept only if σ > 1e-9 rad/ps: equal velocities give σ = 0, and
+ * velocities equal by symmetry give a σ of rounding noise (~1e-15) whose 1/σ weight is meaningless.
  * Acoustic modes at Γ (q index 0, branches 0..2) are excluded as the mode and as partners.
  * Units: ω rad/ps, e dimensionless, Φ eV/Å^k, masses amu, Γ ps^-1 (C3, C4 come from Python).
  */
@@ -139,6 +143,12 @@ static double sigma_of(const fc4o_problem *p, int ma, int mb) {
         s = s + t * t;
     }
     return p->sigma * sqrt(s / 6.0);
+}
+
+/* σ usable as a Gaussian width: any fixed σ > 0; an adaptive σ above the noise floor */
+#define ADAPTIVE_SIGMA_MIN 1e-9
+static int width_ok(const fc4o_problem *p, double sg) {
+    return p->sigma_adaptive ? sg > ADAPTIVE_SIGMA_MIN : sg > 0.0;
 }
 
 static double gaussian(double delta, double sigma) {
@@ -295,7 +305,7 @@ static void enumerate(const fc4o_problem *p, int ch, int m0, int qp_limit, visit
                     int m2 = q2 * nb + j2;
                     double sg = sigma_of(p, m1, m2);
                     double d = delta_of(ch, w0, p->omega[m1], p->omega[m2], 0.0);
-                    if (fabs(d) <= 2.0 * sg) {
+                    if (width_ok(p, sg) && fabs(d) <= 2.0 * sg) {
                         unsigned long long word = ((unsigned long long)m1) * nb + j2;
                         f(ctx, p, ch, m0, m1, m2, -1, d, sg, word);
                     }
@@ -318,7 +328,7 @@ static void enumerate(const fc4o_problem *p, int ch, int m0, int qp_limit, visit
                             int m3 = q3 * nb + j3;
                             double sg = sigma_of(p, m2, m3);
                             double d = delta_of(ch, w0, p->omega[m1], p->omega[m2], p->omega[m3]);
-                            if (fabs(d) <= 2.0 * sg) {
+                            if (width_ok(p, sg) && fabs(d) <= 2.0 * sg) {
                                 unsigned long long word =
                                     (((unsigned long long)m1 * N + q2) * nb + j2) * nb + j3;
                                 f(ctx, p, ch, m0, m1, m2, m3, d, sg, word);

@@ -226,8 +226,10 @@ class Engine:
 
     # -- rates -------------------------------------------------------------------------------
     def rates(self, T: float, sigma_thz: float, channel_mask: int = 31, q_subset=None,
-              out=None, stream=None):
-        """Γ, WP (float64) and kept counts (int64) as [5, n_modes] CUDA tensors."""
+              out=None, stream=None, adaptive: bool = False):
+        """Γ, WP (float64) and kept counts (int64) as [5, n_modes] CUDA tensors.  ``sigma_thz`` is
+        the fixed Gaussian width in THz, or with ``adaptive=True`` the scale factor s of the
+        adaptive width σ = s sqrt(Σ_k ((Δv . b_k) / n_k)² / 6)."""
         import torch
         qs = None if q_subset is None else _np(q_subset, np.int32)
         nm = (self.nq if qs is None else qs.size) * self.nb
@@ -237,7 +239,7 @@ class Engine:
                    torch.empty((5, nm), dtype=torch.float64, device=dev),
                    torch.empty((5, nm), dtype=torch.int64, device=dev))
         g, wp, cnt = out
-        self._check(self.lib.fc4_rates(self.ctx, float(T), 0, float(sigma_thz), int(channel_mask),
+        self._check(self.lib.fc4_rates(self.ctx, float(T), 1 if adaptive else 0, float(sigma_thz), int(channel_mask),
                                        None if qs is None else _ptr(qs), 0 if qs is None else qs.size,
                                        _tptr(g), _tptr(wp), _tptr(cnt), _stream(stream)))
         return g, wp, cnt
@@ -319,9 +321,9 @@ def _autograd():
         Forward: fc4_update_anharmonic + fc4_rates.  Backward: fc4_rates_backward."""
 
         @staticmethod
-        def forward(ctx, phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset):
+        def forward(ctx, phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset, adaptive):
             engine.update_anharmonic(phi3.detach().cpu().numpy(), phi4.detach().cpu().numpy())
-            g, _, _ = engine.rates(T, sigma_thz, channel_mask, q_subset=q_subset)
+            g, _, _ = engine.rates(T, sigma_thz, channel_mask, q_subset=q_subset, adaptive=adaptive)
             ctx.engine = engine
             ctx.dev3, ctx.dev4 = phi3.device, phi4.device
             return g
@@ -331,7 +333,7 @@ def _autograd():
             d3, d4 = ctx.engine.backward(grad_gamma.contiguous().to(torch.float64))
             d3 = d3.to(ctx.dev3) if d3 is not None else None
             d4 = d4.to(ctx.dev4) if d4 is not None else None
-            return d3, d4, None, None, None, None, None
+            return d3, d4, None, None, None, None, None, None
 
     class Kappa(torch.autograd.Function):
         """κ (3x3) as a function of Γ [5, N*nb].  Backward: fc4_kappa_backward."""
@@ -351,10 +353,10 @@ def _autograd():
     return Rates, Kappa
 
 
-def rates_fn(phi3, phi4, engine, T, sigma_thz, channel_mask=31, q_subset=None):
+def rates_fn(phi3, phi4, engine, T, sigma_thz, channel_mask=31, q_subset=None, adaptive=False):
     """Differentiable Γ(Φ3, Φ4) (see ``_autograd``)."""
     Rates, _ = _autograd()
-    return Rates.apply(phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset)
+    return Rates.apply(phi3, phi4, engine, T, sigma_thz, channel_mask, q_subset, adaptive)
 
 
 def kappa_fn(gamma, engine, T, channel_mask=31):

@@ -12,6 +12,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfc4.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+         "-Xcompiler", "-ffp-contract=off",      # host arithmetic (reciprocal vectors) as written
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 

@@ -53,12 +53,14 @@ struct fc4_ctx {
     std::vector<void *> owned;
     std::vector<int> perm4;                 // device cluster slot -> input cluster index
     std::vector<double> om_host;            // current ω (for the prefilter bound)
+    double vmax = 0.0;                      // max |v| over modes (adaptive prefilter bound)
     // writable views of the tables
     double *om = nullptr, *vel = nullptr, *eig = nullptr, *invw = nullptr, *occ = nullptr;
     double *phi3 = nullptr, *phi4 = nullptr;
     float *om32 = nullptr, *om32lo = nullptr, *invw32 = nullptr, *occ32 = nullptr, *phi4_32 = nullptr;
     double2 *ev = nullptr;
     float2 *ev32 = nullptr;
+    float4 *vp32 = nullptr, *vp32lo = nullptr;
     unsigned *vmask = nullptr;
     int *err = nullptr;
     double occ_T = -1.0;
@@ -81,7 +83,8 @@ struct fc4_ctx {
     std::vector<int> modes_on_device;      // content of `modes` (skip re-uploading an unchanged list)
     // last rates call
     bool have_last = false;
-    double last_T = 300.0, last_sigma = 2.0 * kPi * 0.1;
+    double last_T = 300.0, last_sigma = 0.1;   // σ in THz, or the scale s if adaptive
+    bool last_adaptive = false;
     int last_mask = 0;
     std::vector<int> last_modes;
     std::string last_error;
@@ -154,10 +157,16 @@ fc4_status check_ifc(const fc4_ifc *f, int order, int n_atoms, bool required, co
 // Rebuild the derived mode tables after ω / e changed (also zeroes the excluded ω).
 fc4_status refresh_modes(fc4_ctx *c) {
     FC4_CUDA(c, fc4::launch_mode_tables(c->t, c->om, c->om32, c->om32lo, c->ev32, c->ev, c->vmask,
-                                        c->invw, c->invw32, 0));
-    c->om_host.assign((size_t)c->t.N * c->t.nb, 0.0);
-    FC4_CUDA(c, cudaMemcpy(c->om_host.data(), c->om, c->om_host.size() * sizeof(double),
-                           cudaMemcpyDeviceToHost));
+                                        c->invw, c->invw32, c->vp32, c->vp32lo, 0));
+    const size_t nm = (size_t)c->t.N * c->t.nb;
+    c->om_host.assign(nm, 0.0);
+    FC4_CUDA(c, cudaMemcpy(c->om_host.data(), c->om, nm * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> v(3 * nm);
+    FC4_CUDA(c, cudaMemcpy(v.data(), c->vel, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    c->vmax = 0.0;
+    for (size_t i = 0; i < nm; ++i)
+        c->vmax = std::max(c->vmax, std::sqrt(v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] +
+                                              v[3 * i + 2] * v[3 * i + 2]));
     c->occ_T = -1.0;
     return FC4_OK;
 }
@@ -192,12 +201,52 @@ fc4_status ensure_occupations(fc4_ctx *c, double T, cudaStream_t s) {
 // Prefilter thresholds: |Δ32 - Δ64| <= 13 u ω_max (u = 2^-24; three roundings of the inputs'
 // partial sums plus four input roundings); margin 32 u ω_max, doubled to cover the rounding of
 // the thresholds themselves.
-void prefilter(const fc4_ctx *c, double two_sigma, float *lo, float *hi) {
+double prefilter_eps(const fc4_ctx *c) {
     double wmax = 0.0;
     for (double w : c->om_host) wmax = std::max(wmax, std::fabs(w));
-    const double eps = 32.0 * std::ldexp(1.0, -24) * wmax;
+    return 32.0 * std::ldexp(1.0, -24) * wmax;
+}
+
+void prefilter(const fc4_ctx *c, double two_sigma, float *lo, float *hi) {
+    const double eps = prefilter_eps(c);
     *lo = std::nextafter((float)(two_sigma - 2.0 * eps), 0.0f);
     *hi = std::nextafter((float)(two_sigma + 2.0 * eps), 1e30f);
+}
+
+// Window and Gaussian parameters of a rates call: fixed σ = 2π sigma_value rad/ps, or adaptive
+// σ = s |ΔP| / sqrt(6) with s = sigma_value.  For the adaptive prefilter, Q = max|v| max_k |b_k| / n_k
+// bounds every |P_k| and the FP64 rounding of the exact σ (<= 2^-50 Q per component); the margins
+// are those stated with the kernels' window test.
+void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_value) {
+    a.adaptive = adaptive ? 1 : 0;
+    if (!adaptive) {
+        const double sigma = 2.0 * kPi * sigma_value;
+        a.two_sigma = 2.0 * sigma;
+        a.inv_sigma2 = 1.0 / (sigma * sigma);
+        a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
+        a.inv_sigma2_32 = (float)a.inv_sigma2;
+        a.gnorm32 = (float)a.gnorm;
+        prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+        return;
+    }
+    const double u = std::ldexp(1.0, -24);
+    double bmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double *b = c->t.recip + 3 * k;
+        bmax = std::max(bmax, std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) / c->t.mesh[k]);
+    }
+    const double Q = c->vmax * bmax;
+    const double c2 = 2.0 * sigma_value / std::sqrt(6.0);
+    a.ad_scale = sigma_value;
+    a.ad_c32 = (float)c2;
+    a.ad_s32 = (float)(sigma_value / std::sqrt(6.0));
+    a.ad_rlo = (float)(1.0 - 32.0 * u);
+    a.ad_rhi = (float)(1.0 + 32.0 * u);
+    a.ad_e0 = std::nextafter((float)(2.0 * prefilter_eps(c) + std::ldexp(c2 * Q, -40)), 1e30f);
+    a.ad_gmin = std::nextafter((float)((2.0 * fc4::kAdaptiveSigmaMin + std::ldexp(c2 * Q, -40)) * (1.0 + 64.0 * u)), 1e30f);
+    a.two_sigma = 0.0;                  // unused with adaptive σ; thresholds that keep nothing
+    a.lo32 = -1.0f;
+    a.hi32 = -1.0f;
 }
 
 }  // namespace
@@ -270,6 +319,22 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     for (int k = 0; k < 3; ++k) t.mesh[k] = mesh[k];
     t.L = lcm_i(lcm_i(mesh[0], mesh[1]), mesh[2]);
     c->volume = vol;
+    {   // reciprocal vectors b_1 = 2π (a_2 x a_3) / (a_1 . (a_2 x a_3)) and cyclic, left to right
+        const double *a0 = A, *a1 = A + 3, *a2 = A + 6;
+        double cr[3][3];
+        auto cross = [](const double *x, const double *y, double *r) {
+            r[0] = x[1] * y[2] - x[2] * y[1];
+            r[1] = x[2] * y[0] - x[0] * y[2];
+            r[2] = x[0] * y[1] - x[1] * y[0];
+        };
+        cross(a1, a2, cr[0]);
+        cross(a2, a0, cr[1]);
+        cross(a0, a1, cr[2]);
+        const double v = a0[0] * cr[0][0] + a0[1] * cr[0][1] + a0[2] * cr[0][2];
+        const double f = 2.0 * kPi / v;
+        for (int i = 0; i < 3; ++i)
+            for (int x = 0; x < 3; ++x) t.recip[3 * i + x] = f * cr[i][x];
+    }
     const int L = t.L;
 
     // mesh coordinates and roots of unity
@@ -434,6 +499,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     FC4_TRY(dalloc(c, &c->occ, nm));
     FC4_TRY(dalloc(c, &c->occ32, nm));
     FC4_TRY(dalloc(c, &c->vmask, (size_t)N));
+    FC4_TRY(dalloc(c, &c->vp32, nm));
+    FC4_TRY(dalloc(c, &c->vp32lo, nm));
     FC4_TRY(dalloc(c, &c->err, 1));
     FC4_TRY(cudaMemset(c->err, 0, sizeof(int)));
     t.om = c->om;
@@ -443,6 +510,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     t.ev = c->ev;
     t.ev32 = c->ev32;
     t.vmask = c->vmask;
+    t.vp32 = c->vp32;
+    t.vp32lo = c->vp32lo;
     t.occ = c->occ;
     t.occ32 = c->occ32;
     t.invw = c->invw;
@@ -506,8 +575,9 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
                      double *wp_out, long long *counts_out, void *stream) {
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!(T_K > 0.0) || !std::isfinite(T_K)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
-    if (sigma_adaptive) return fail(c, FC4_ERR_INVALID, "adaptive broadening is not supported by fc4_rates");
-    if (!(sigma_value > 0.0) || !std::isfinite(sigma_value)) return fail(c, FC4_ERR_INVALID, "sigma must be > 0");
+    if (sigma_adaptive != 0 && sigma_adaptive != 1) return fail(c, FC4_ERR_INVALID, "sigma_adaptive must be 0 or 1");
+    if (!(sigma_value > 0.0) || !std::isfinite(sigma_value))
+        return fail(c, FC4_ERR_INVALID, sigma_adaptive ? "the adaptive scale must be > 0" : "sigma must be > 0");
     if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
     const int N = c->t.N, nb = c->t.nb;
     std::vector<int> modes;
@@ -557,16 +627,10 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     }
     fc4_status st = ensure_occupations(c, T_K, s);
     if (st != FC4_OK) return st;
-    const double sigma = 2.0 * kPi * sigma_value;
     fc4::RateArgs a{};
     a.n_modes = nm;
     a.modes = c->modes;
-    a.two_sigma = 2.0 * sigma;
-    a.inv_sigma2 = 1.0 / (sigma * sigma);
-    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
-    a.inv_sigma2_32 = (float)a.inv_sigma2;
-    a.gnorm32 = (float)a.gnorm;
-    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    set_window(c, a, sigma_adaptive != 0, sigma_value);
     a.part_g = c->part_g;
     a.part_wp = c->part_wp;
     a.part_n = c->part_n;
@@ -650,7 +714,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     }
     c->have_last = true;
     c->last_T = T_K;
-    c->last_sigma = sigma;
+    c->last_sigma = sigma_value;
+    c->last_adaptive = sigma_adaptive != 0;
     c->last_mask = channel_mask;
     c->last_modes = modes;
     return FC4_OK;
@@ -663,9 +728,8 @@ fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *
     if (mode < 0 || mode >= c->t.N * c->t.nb) return fail(c, FC4_ERR_INVALID, "mode out of range");
     if (cap < 0 || (cap > 0 && !words)) return fail(c, FC4_ERR_INVALID, "bad words / cap");
     const long long n_thr = channel < 2 ? (long long)c->t.N * c->t.nb : (long long)c->t.N * c->t.nb * c->t.N;
-    const double two_sigma = 2.0 * c->last_sigma;
-    float lo, hi;
-    prefilter(c, two_sigma, &lo, &hi);
+    fc4::RateArgs a{};
+    set_window(c, a, c->last_adaptive, c->last_sigma);
     int *d_counts = nullptr;
     long long *d_off = nullptr;
     unsigned long long *d_words = nullptr;
@@ -675,7 +739,7 @@ fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *
         cudaFree(d_words);
     };
     cudaError_t e = cudaMalloc(&d_counts, n_thr * sizeof(int));
-    if (e == cudaSuccess) e = fc4::launch_count_processes(c->t, channel, mode, two_sigma, lo, hi, d_counts, 0);
+    if (e == cudaSuccess) e = fc4::launch_count_processes(c->t, a, channel, mode, d_counts, 0);
     std::vector<int> counts(n_thr);
     if (e == cudaSuccess) e = cudaMemcpy(counts.data(), d_counts, n_thr * sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "fc4_processes count"); }
@@ -687,7 +751,7 @@ fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *
         e = cudaMalloc(&d_off, n_thr * sizeof(long long));
         if (e == cudaSuccess) e = cudaMalloc(&d_words, total * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemcpy(d_off, off.data(), n_thr * sizeof(long long), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = fc4::launch_write_processes(c->t, channel, mode, two_sigma, lo, hi, d_off, d_words, 0);
+        if (e == cudaSuccess) e = fc4::launch_write_processes(c->t, a, channel, mode, d_off, d_words, 0);
         if (e == cudaSuccess)
             e = cudaMemcpy(words, d_words, std::min(cap, total) * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "fc4_processes write"); }
@@ -753,16 +817,10 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
     }
     fc4_status st = ensure_occupations(c, c->last_T, s);
     if (st != FC4_OK) return st;
-    const double sigma = c->last_sigma;
     fc4::RateArgs a{};
     a.n_modes = nm;
     a.modes = c->modes;
-    a.two_sigma = 2.0 * sigma;
-    a.inv_sigma2 = 1.0 / (sigma * sigma);
-    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
-    a.inv_sigma2_32 = (float)a.inv_sigma2;
-    a.gnorm32 = (float)a.gnorm;
-    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    set_window(c, a, c->last_adaptive, c->last_sigma);
     const double N = (double)c->t.N;
     bool first3 = true, first4 = true;
     for (int ch = 0; ch < 5; ++ch) {
@@ -953,16 +1011,10 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
     FC4_CUDA(c, cudaGetLastError());
     fc4_status st = ensure_occupations(c, T_K, s);
     if (st != FC4_OK) return st;
-    const double sigma = 2.0 * kPi * sigma_value;
     fc4::RateArgs a{};
     a.n_modes = (int)nm;
     a.modes = d_modes;
-    a.two_sigma = 2.0 * sigma;
-    a.inv_sigma2 = 1.0 / (sigma * sigma);
-    a.gnorm = 1.0 / (sigma * std::sqrt(kPi));
-    a.inv_sigma2_32 = (float)a.inv_sigma2;
-    a.gnorm32 = (float)a.gnorm;
-    prefilter(c, a.two_sigma, &a.lo32, &a.hi32);
+    set_window(c, a, false, sigma_value);
     a.part_g = part_g;
     a.part_wp = part_wp;
     a.part_n = part_n;

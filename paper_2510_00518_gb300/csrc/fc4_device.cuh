@@ -110,6 +110,37 @@ __device__ __forceinline__ R occupation_factor(int ch, R n1, R n2, R n3) {
     }
 }
 
+// ------------------------------------------------------------------------------ adaptive width
+
+// Adaptive Gaussian width of two modes from their group velocities v_a, v_b (Å rad/ps), the
+// reciprocal vectors b (rows, 1/Å) and the mesh n:
+//   σ = s sqrt(Σ_k ((Δv . b_k) / n_k)² / 6),  Δv = v_a - v_b,
+// in IEEE FP64 with every operation rounded to nearest in the order written (never contracted or
+// reassociated), so that the window decision σ > 0 and |Δ| <= 2σ is reproducible bit for bit.
+__device__ __forceinline__ double sigma_adaptive_exact(const double *va, const double *vb, const double *b,
+                                                       const int *n, double s) {
+    const double d0 = __dsub_rn(va[0], vb[0]), d1 = __dsub_rn(va[1], vb[1]), d2 = __dsub_rn(va[2], vb[2]);
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double x = __dadd_rn(__dadd_rn(__dmul_rn(d0, b[3 * k]), __dmul_rn(d1, b[3 * k + 1])),
+                             __dmul_rn(d2, b[3 * k + 2]));
+        x = __ddiv_rn(x, (double)n[k]);
+        acc = __dadd_rn(acc, __dmul_rn(x, x));
+    }
+    return __dmul_rn(s, __dsqrt_rn(__ddiv_rn(acc, 6.0)));
+}
+
+// |ΔP| for the FP32 prefilter and the mixed-precision weight, where P_k = (v . b_k) / n_k is stored
+// per mode as an FP32 hi/lo pair: the hi parts of two close velocities subtract exactly, so the
+// difference is accurate to a few ulp of itself plus ~2^-45 max|P|.
+__device__ __forceinline__ float vel_diff_norm32(float4 ha, float4 la, float4 hb, float4 lb) {
+    const float x = (ha.x - hb.x) + (la.x - lb.x);
+    const float y = (ha.y - hb.y) + (la.y - lb.y);
+    const float z = (ha.z - hb.z) + (la.z - lb.z);
+    return __fsqrt_rn(x * x + y * y + z * z);
+}
+
 // ------------------------------------------------------------------------------ block helpers
 
 // Exclusive scan of one int per thread across the block (blockDim.x a multiple of 32, <= 1024).

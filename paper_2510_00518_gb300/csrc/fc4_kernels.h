@@ -9,6 +9,7 @@ namespace fc4 {
 
 constexpr int kMaxAtoms = 8;      // nb <= 24: branch masks fit in 32 bits
 constexpr int kGroups = kMaxAtoms * kMaxAtoms + 1;   // (leg-2 atom, leg-3 atom) groups + 1
+constexpr double kAdaptiveSigmaMin = 1e-9;           // rad/ps: adaptive widths at or below are noise
 
 // Device tables of one context (all pointers are device memory).
 struct Tables {
@@ -26,6 +27,9 @@ struct Tables {
     const double2 *ev;           // [N][nb comp][nb branch]
     const float2 *ev32;          // [N][nb][nb]
     const unsigned *vmask;       // [N] bit j set iff mode (q, j) takes part
+    const float4 *vp32;          // [N*nb] P_k = (v . b_k) / n_k, k = 1..3 (rad/ps), FP32 hi parts
+    const float4 *vp32lo;        // [N*nb] P_k - hi, FP32 (lo parts)
+    double recip[9];             // reciprocal vectors b_k (rows, 1/Å), a_i . b_k = 2π δ_ik
     // occupations at the current T
     const double *occ;           // [N*nb]
     const float *occ32;          // [N*nb]
@@ -71,6 +75,15 @@ struct RateArgs {
     void *wbuf;                  // optional scratch for the tiled 4ph path (W per (λ, q')); may be NULL
     size_t wbuf_bytes;
     int w_reuse;                 // 1: wbuf already holds W of every mode for this channel's sign s1
+    // adaptive broadening: σ of a process from the velocities of the two legs its free partner
+    // sum moves together (3ph: λ', λ''; 4ph: λ'', λ'''), σ = s |ΔP| / sqrt(6)
+    int adaptive;
+    double ad_scale;             // s
+    float ad_c32;                // 2 s / sqrt(6): 2σ ≈ ad_c32 |ΔP| (FP32)
+    float ad_s32;                // s / sqrt(6)
+    float ad_rlo, ad_rhi;        // prefilter: keep if |Δ32| <= ad_rlo 2σ32 - ad_e0,
+    float ad_e0;                 //   reject if |Δ32| > ad_rhi 2σ32 + ad_e0, else exact FP64
+    float ad_gmin;               // sure keep also needs 2σ32 > ad_gmin (σ above the noise floor)
 };
 
 // launchers (stream-ordered; return cudaGetLastError())
@@ -89,7 +102,7 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
                             int *err, cudaStream_t s);
 cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
                                float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
-                               float *invw32, cudaStream_t s);
+                               float *invw32, float4 *vp32, float4 *vp32lo, cudaStream_t s);
 cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ, float *occ32,
                                cudaStream_t s);
 cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4, float2 *P4_32,
@@ -103,10 +116,9 @@ cudaError_t launch_adjoint(const Tables &t, const RateArgs &a, int ch, const dou
                            double *part, cudaStream_t s);
 cudaError_t launch_sum_slices(int n_slices, int n, const double *part, double *out, int accumulate,
                               cudaStream_t s);
-cudaError_t launch_count_processes(const Tables &t, int ch, int mode, double two_sigma,
-                                   float lo32, float hi32, int *counts, cudaStream_t s);
-cudaError_t launch_write_processes(const Tables &t, int ch, int mode, double two_sigma,
-                                   float lo32, float hi32, const long long *offsets,
-                                   unsigned long long *words, cudaStream_t s);
+cudaError_t launch_count_processes(const Tables &t, const RateArgs &a, int ch, int mode, int *counts,
+                                   cudaStream_t s);
+cudaError_t launch_write_processes(const Tables &t, const RateArgs &a, int ch, int mode,
+                                   const long long *offsets, unsigned long long *words, cudaStream_t s);
 
 }  // namespace fc4

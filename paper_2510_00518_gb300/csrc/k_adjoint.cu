@@ -16,8 +16,7 @@
 //
 // Three-phonon: one block per mode λ; processes are compacted per round in the same way and
 // the owner of each Φ3 entry adds 2 Re(G conj(V) phase_c e_λ e^s' e*'' / sqrt(m)) in order.
-#include "fc4_device.cuh"
-#include "fc4_kernels.h"
+#include "fc4_window.cuh"
 
 namespace fc4 {
 
@@ -119,7 +118,11 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                                 if (!((v2 >> j2) & 1u)) continue;
                                 const float ad = fabsf((base32 + (float)s2 * t.om32[q2 * NB + j2]) - t.om32[q3 * NB + j3]);
                                 bool keep;
-                                if (ad <= a.lo32) keep = true;
+                                if (a.adaptive) {
+                                    const int mm2 = q2 * NB + j2, mm3 = q3 * NB + j3;
+                                    const int w = window_adaptive32(a, ad, two_sigma32(t, a, mm2, mm3));
+                                    keep = w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, m1, mm2, mm3, mm2, mm3));
+                                } else if (ad <= a.lo32) keep = true;
                                 else if (ad > a.hi32) keep = false;
                                 else keep = fabs(delta_exact(ch, w0, w1, t.om[q2 * NB + j2], t.om[q3 * NB + j3])) <= a.two_sigma;
                                 m |= (unsigned)keep << j2;
@@ -177,7 +180,8 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                             for (int c = 0; c < NA; ++c)
                                 for (int g = 0; g < 3; ++g) V = cfma(e2[3 * c + g], Y[c][g], V);
                             const double d = delta_exact(ch, w0, w1, t.om[m2], t.om[m3]);
-                            const double gs = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                            const double gs = a.adaptive ? gauss_adaptive(t, a, d, m2, m3)
+                                                         : exp(-(d * d) * a.inv_sigma2) * a.gnorm;
                             const double w = (ch == 4 ? 1.0 / 6.0 : 0.5) *
                                              occupation_factor<double>(ch, t.occ[m1], t.occ[m2], t.occ[m3]) * gs *
                                              t.invw[m0] * t.invw[m1] * t.invw[m2] * t.invw[m3];
@@ -264,7 +268,9 @@ adj3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
             for (int j1 = 0; j1 < NB; ++j1)
                 for (int j2 = 0; j2 < NB; ++j2)
                     if (((v1 >> j1) & (v2 >> j2) & 1u) &&
-                        fabs(delta_exact(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], 0.0)) <= a.two_sigma)
+                        (a.adaptive ? window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2, -1,
+                                                            q1 * NB + j1, q2 * NB + j2)
+                                    : fabs(delta_exact(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], 0.0)) <= a.two_sigma))
                         kept |= 1ull << (j1 * NB + j2);
         }
         if (threadIdx.x == 0) s_max = 0;
@@ -300,7 +306,7 @@ adj3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                     V = crfma(t.c3_ism[c], cmul(t.rt[idx], acc), V);
                 }
                 const double d = delta_exact(ch, w0, t.om[m1], t.om[m2], 0.0);
-                const double gs = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                const double gs = a.adaptive ? gauss_adaptive(t, a, d, m1, m2) : exp(-(d * d) * a.inv_sigma2) * a.gnorm;
                 const double w = sym * occupation_factor<double>(ch, t.occ[m1], t.occ[m2], 0.0) * gs *
                                  t.invw[m0] * t.invw[m1] * t.invw[m2];
                 it.m1 = m1;

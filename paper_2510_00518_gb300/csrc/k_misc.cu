@@ -1,8 +1,7 @@
 // k_misc.cu - the harmonic prelude (batched FP64 Jacobi eigensolver of D(q), Hellmann-Feynman
 // group velocities), per-mode tables, occupations, key phase tables, the deterministic reduction
 // of per-(λ, q') partials into Γ / WP / counts, the RTA conductivity, and process lists.
-#include "fc4_device.cuh"
-#include "fc4_kernels.h"
+#include "fc4_window.cuh"
 
 namespace fc4 {
 
@@ -174,8 +173,13 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
 
 // ------------------------------------------------------------------------------ tables
 
-__global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float *om32lo, float2 *ev32,
-                                   const double2 *ev, unsigned *vmask, double *invw, float *invw32) {
+// Per-mode tables derived from ω, e and v: FP32 hi/lo splits of ω, 1/ω, FP32 eigenvectors, the
+// participation mask, and the velocity projections P_k = (v . b_k) / n_k (hi/lo FP32) of the
+// adaptive width.
+__global__ void mode_tables_kernel(const __grid_constant__ Tables t, double *om, float *om32, float *om32lo,
+                                   float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
+                                   float *invw32, float4 *vp32, float4 *vp32lo) {
+    const int N = t.N, nb = t.nb;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nm = (long long)N * nb;
     if (i < nm) {
@@ -186,6 +190,16 @@ __global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float
         om32lo[i] = (float)(w - (double)(float)w);
         invw[i] = w > 0.0 ? 1.0 / w : 0.0;
         invw32[i] = w > 0.0 ? (float)(1.0 / w) : 0.0f;
+        const double *v = t.vel + 3 * i;
+        float h[3], l[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double p = (v[0] * t.recip[3 * k] + v[1] * t.recip[3 * k + 1] + v[2] * t.recip[3 * k + 2]) / t.mesh[k];
+            h[k] = (float)p;
+            l[k] = (float)(p - (double)h[k]);
+        }
+        vp32[i] = make_float4(h[0], h[1], h[2], 0.0f);
+        vp32lo[i] = make_float4(l[0], l[1], l[2], 0.0f);
     }
     if (i < nm * nb) {
         const double2 e = ev[i];
@@ -201,10 +215,10 @@ __global__ void mode_tables_kernel(int N, int nb, double *om, float *om32, float
 
 cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
                                float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
-                               float *invw32, cudaStream_t s) {
+                               float *invw32, float4 *vp32, float4 *vp32lo, cudaStream_t s) {
     const long long n = (long long)t.N * t.nb * t.nb;
-    mode_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.N, t.nb, om, om32, om32lo, ev32,
-                                                                    ev, vmask, invw, invw32);
+    mode_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, om, om32, om32lo, ev32, ev, vmask, invw,
+                                                                    invw32, vp32, vp32lo);
     return cudaGetLastError();
 }
 
@@ -393,26 +407,30 @@ cudaError_t launch_unpermute(int nc, int width, const int *perm, const double *i
 // ------------------------------------------------------------------------------ process lists
 
 // The same window decision as the rate kernels: exact FP64 for 3ph; FP32 prefilter with a proven
-// bound plus exact FP64 for the ambiguous band for 4ph.  One thread per (q', j') (3ph) or
-// (q', j', q'') (4ph), in canonical order; counts first, then words at scanned offsets.
-__device__ __forceinline__ bool keep3(const Tables &t, int ch, int m0, int m1, int m2, double two_sigma) {
-    return fabs(delta_exact(ch, t.om[m0], t.om[m1], t.om[m2], 0.0)) <= two_sigma;
+// bound plus exact FP64 for the ambiguous band for 4ph (fixed or adaptive σ).  One thread per
+// (q', j') (3ph) or (q', j', q'') (4ph), in canonical order; counts first, then words at scanned
+// offsets.
+__device__ __forceinline__ bool keep3(const Tables &t, const RateArgs &a, int ch, int m0, int m1, int m2) {
+    if (a.adaptive) return window_exact_adaptive(t, a, ch, m0, m1, m2, -1, m1, m2);
+    return fabs(delta_exact(ch, t.om[m0], t.om[m1], t.om[m2], 0.0)) <= a.two_sigma;
 }
 
-__device__ __forceinline__ bool keep4(const Tables &t, int ch, int m0, int m1, int m2, int m3,
-                                      double two_sigma, float lo, float hi) {
+__device__ __forceinline__ bool keep4(const Tables &t, const RateArgs &a, int ch, int m0, int m1, int m2, int m3) {
     const int s1 = (ch == 4) ? -1 : 1, s2 = (ch == 2) ? 1 : -1;
     const float base = t.om32[m0] + (float)s1 * t.om32[m1];
     const float ad = fabsf((base + (float)s2 * t.om32[m2]) - t.om32[m3]);
-    if (ad <= lo) return true;
-    if (ad > hi) return false;
-    return fabs(delta_exact(ch, t.om[m0], t.om[m1], t.om[m2], t.om[m3])) <= two_sigma;
+    if (a.adaptive) {
+        const int w = window_adaptive32(a, ad, two_sigma32(t, a, m2, m3));
+        return w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, m1, m2, m3, m2, m3));
+    }
+    if (ad <= a.lo32) return true;
+    if (ad > a.hi32) return false;
+    return fabs(delta_exact(ch, t.om[m0], t.om[m1], t.om[m2], t.om[m3])) <= a.two_sigma;
 }
 
 template <bool WRITE>
-__global__ void processes_kernel(const __grid_constant__ Tables t, int ch, int m0, double two_sigma,
-                                 float lo, float hi, int *counts, const long long *offsets,
-                                 unsigned long long *words) {
+__global__ void processes_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
+                                 int m0, int *counts, const long long *offsets, unsigned long long *words) {
     const int nb = t.nb, N = t.N;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = m0 / nb;
@@ -428,7 +446,7 @@ __global__ void processes_kernel(const __grid_constant__ Tables t, int ch, int m
         if (((t.vmask[q0] >> (m0 - q0 * nb)) & 1u) && ((t.vmask[q1] >> j1) & 1u))
             for (int j2 = 0; j2 < nb; ++j2) {
                 if (!((t.vmask[q2] >> j2) & 1u)) continue;
-                if (keep3(t, ch, m0, m1, q2 * nb + j2, two_sigma)) {
+                if (keep3(t, a, ch, m0, m1, q2 * nb + j2)) {
                     if (WRITE) words[o + n] = (unsigned long long)m1 * nb + j2;
                     ++n;
                 }
@@ -448,7 +466,7 @@ __global__ void processes_kernel(const __grid_constant__ Tables t, int ch, int m
                 if (!((t.vmask[q2] >> j2) & 1u)) continue;
                 for (int j3 = 0; j3 < nb; ++j3) {
                     if (!((t.vmask[q3] >> j3) & 1u)) continue;
-                    if (keep4(t, ch, m0, m1, q2 * nb + j2, q3 * nb + j3, two_sigma, lo, hi)) {
+                    if (keep4(t, a, ch, m0, m1, q2 * nb + j2, q3 * nb + j3)) {
                         if (WRITE)
                             words[o + n] = (((unsigned long long)m1 * N + q2) * nb + j2) * nb + j3;
                         ++n;
@@ -463,20 +481,17 @@ static long long process_threads(const Tables &t, int ch) {
     return ch < 2 ? (long long)t.N * t.nb : (long long)t.N * t.nb * t.N;
 }
 
-cudaError_t launch_count_processes(const Tables &t, int ch, int mode, double two_sigma,
-                                   float lo32, float hi32, int *counts, cudaStream_t s) {
+cudaError_t launch_count_processes(const Tables &t, const RateArgs &a, int ch, int mode, int *counts,
+                                   cudaStream_t s) {
     const long long n = process_threads(t, ch);
-    processes_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, ch, mode, two_sigma, lo32,
-                                                                       hi32, counts, nullptr, nullptr);
+    processes_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, a, ch, mode, counts, nullptr, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_write_processes(const Tables &t, int ch, int mode, double two_sigma,
-                                   float lo32, float hi32, const long long *offsets,
-                                   unsigned long long *words, cudaStream_t s) {
+cudaError_t launch_write_processes(const Tables &t, const RateArgs &a, int ch, int mode,
+                                   const long long *offsets, unsigned long long *words, cudaStream_t s) {
     const long long n = process_threads(t, ch);
-    processes_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, ch, mode, two_sigma, lo32,
-                                                                      hi32, nullptr, offsets, words);
+    processes_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, a, ch, mode, nullptr, offsets, words);
     return cudaGetLastError();
 }
 

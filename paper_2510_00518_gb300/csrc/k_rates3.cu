@@ -9,15 +9,15 @@
 // thread then evaluates one process:
 //   V3^s = Σ_c exp(-i q.R2) exp(i s q'.(R1 - R2)) Σ_βγ Φ~_c[β][γ] e^s_λ'(bβ) e*_λ''(cγ)
 // (the phase of exp(i(s q'.R1 - q''.R2)) with q'' = q + s q'), its weight, and w |V3|².
-// Compaction keeps the rare kept processes from serialising warps.
-#include "fc4_device.cuh"
-#include "fc4_kernels.h"
+// Compaction keeps the rare kept processes from serialising warps.  With adaptive broadening the
+// width of a process comes from v' - v'' (prefiltered in FP32 the same way, exact FP64 otherwise).
+#include "fc4_window.cuh"
 
 namespace fc4 {
 
 constexpr int kR3Threads = 128;
 
-template <int NA>
+template <int NA, bool ADA>
 __global__ void __launch_bounds__(kR3Threads)
 rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch) {
     constexpr int NB = 3 * NA;
@@ -69,13 +69,20 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                 unsigned kept = 0;
                 if ((v1 >> j1) & 1u) {
                     const float base32 = w0f + (float)s * t.om32[q1 * NB + j1];
+                    const int m1 = q1 * NB + j1;
                     for (int j2 = 0; j2 < NB; ++j2) {
                         if (!((v2 >> j2) & 1u)) continue;
-                        const float ad = fabsf(base32 - t.om32[q2 * NB + j2]);
+                        const int m2 = q2 * NB + j2;
+                        const float ad = fabsf(base32 - t.om32[m2]);
                         bool keep;
-                        if (ad <= a.lo32) keep = true;
-                        else if (ad > a.hi32) keep = false;
-                        else keep = fabs(delta_exact(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], 0.0)) <= a.two_sigma;
+                        if constexpr (ADA) {
+                            const int w = window_adaptive32(a, ad, two_sigma32(t, a, m1, m2));
+                            keep = w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, m1, m2, -1, m1, m2));
+                        } else {
+                            if (ad <= a.lo32) keep = true;
+                            else if (ad > a.hi32) keep = false;
+                            else keep = fabs(delta_exact(ch, w0, t.om[m1], t.om[m2], 0.0)) <= a.two_sigma;
+                        }
                         kept |= (unsigned)keep << j2;
                     }
                 }
@@ -113,7 +120,9 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                         V = cfma(t.rt[idx], u, V);
                     }
                     const double d = delta_exact(ch, w0, t.om[m1], t.om[m2], 0.0);
-                    const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                    double g;
+                    if constexpr (ADA) g = gauss_adaptive(t, a, d, m1, m2);
+                    else g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
                     const double w = sym * occupation_factor<double>(ch, t.occ[m1], t.occ[m2], 0.0) * g *
                                      t.invw[m0] * t.invw[m1] * t.invw[m2];
                     acc_wp += w;
@@ -144,9 +153,10 @@ static cudaError_t launch3(const Tables &t, RateArgs &a, int ch, cudaStream_t s)
     if (a.n_modes == 0) return cudaSuccess;
     const size_t smem = sizeof(double2) * (size_t)t.nc3 * 9 + sizeof(int) * (size_t)t.nc3 +
                         sizeof(unsigned) * (size_t)kR3Threads * NB + 16;
-    cudaError_t e = cudaFuncSetAttribute(rates3_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = a.adaptive ? rates3_kernel<NA, true> : rates3_kernel<NA, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    rates3_kernel<NA><<<a.n_modes, kR3Threads, smem, s>>>(t, a, ch);
+    kern<<<a.n_modes, kR3Threads, smem, s>>>(t, a, ch);
     return cudaGetLastError();
 }
 

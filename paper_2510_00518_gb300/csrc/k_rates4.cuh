@@ -15,8 +15,7 @@
 // block scan, and each item computes Y[cγ] = Σ_r P_r Σ_δ W_r[γδ] e*_λ'''(dδ) once for all its
 // j'' (V = Σ_cγ e^s2_λ''(cγ) Y[cγ]).
 #pragma once
-#include "fc4_device.cuh"
-#include "fc4_kernels.h"
+#include "fc4_window.cuh"
 
 namespace fc4 {
 
@@ -83,11 +82,20 @@ __device__ __forceinline__ float delta_comp(float h0, float l0, float h1, float 
 
 // Window masks of one q'': bit j'' of mask[j'''] is set iff the process is kept.  FP32 prefilter
 // with the proven bound; candidates inside the band are decided by the exact FP64 Δ.
-template <int NB>
+template <int NB, bool ADA>
 __device__ __forceinline__ int window_masks(const Tables &t, const RateArgs &a, int ch, int s2,
-                                            float base32, double w0, double w1, int q2, int q3,
-                                            unsigned (&mask)[NB]) {
+                                            float base32, int m0, int m1, double w0, double w1, int q2,
+                                            int q3, unsigned (&mask)[NB]) {
     const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+    if constexpr (ADA) {
+        int n = 0;
+        for (int j3 = 0; j3 < NB; ++j3) {
+            mask[j3] = ((v3 >> j3) & 1u) ? window_adaptive4_row<NB>(t, a, ch, s2, base32, m0, m1, q2, q3 * NB + j3, v2)
+                                         : 0u;
+            n += (mask[j3] != 0);
+        }
+        return n;
+    }
     float t2[NB], w3f[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
@@ -133,7 +141,7 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-template <typename R, int NA>
+template <typename R, int NA, bool ADA>
 __global__ void __launch_bounds__(128, 4)
 rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch) {
     using C = Cplx<R>;
@@ -229,7 +237,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                     unsigned mask[NB];
-                    if (window_masks<NB>(t, a, ch, s2, base32, w0, w1, q2, q3, mask) > 0) {
+                    if (window_masks<NB, ADA>(t, a, ch, s2, base32, m0, m1, w0, w1, q2, q3, mask) > 0) {
                         if constexpr (XROUTE) {
                             unsigned long long e = (unsigned long long)q2 << 40;
 #pragma unroll
@@ -250,7 +258,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                         const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                                t.mesh[0], t.mesh[1], t.mesh[2]);
                         unsigned mask[NB];
-                        if (window_masks<NB>(t, a, ch, s2, base32, w0, w1, q2, q3, mask) > 0) sQ[off++] = q2;
+                        if (window_masks<NB, ADA>(t, a, ch, s2, base32, m0, m1, w0, w1, q2, q3, mask) > 0) sQ[off++] = q2;
                     }
                 }
                 __syncthreads();
@@ -267,7 +275,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
 #pragma unroll
                         for (int j3 = 0; j3 < NB; ++j3) mask[j3] = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);
                     } else {
-                        window_masks<NB>(t, a, ch, s2, base32, w0, w1, iq2, q3, mask);
+                        window_masks<NB, ADA>(t, a, ch, s2, base32, m0, m1, w0, w1, iq2, q3, mask);
                     }
                     const C *P = P4 + (size_t)iq2 * t.n_keys;
                     C X[XROUTE ? NA : 1][XROUTE ? NA : 1][9];
@@ -351,13 +359,17 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                             R w;
                             if constexpr (sizeof(R) == 8) {
                                 const double d = delta_exact(ch, w0, w1, t.om[m2], t.om[m3]);
-                                const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                                double g;
+                                if constexpr (ADA) g = gauss_adaptive(t, a, d, m2, m3);
+                                else g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
                                 w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
                                     g * invw[m0] * invw[m1] * invw[m2] * iw3;
                             } else {
                                 const float df = delta_comp(t.om32[m0], t.om32lo[m0], t.om32[m1], t.om32lo[m1],
                                                             t.om32[m2], t.om32lo[m2], t.om32[m3], t.om32lo[m3], s1, s2);
-                                const float g = __expf(-(df * df) * (float)a.inv_sigma2) * (float)a.gnorm;
+                                float g;
+                                if constexpr (ADA) g = gauss_adaptive32(t, a, df, m2, m3);
+                                else g = __expf(-(df * df) * a.inv_sigma2_32) * a.gnorm32;
                                 w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
                                     (invw[m0] * invw[m1]) * (invw[m2] * iw3);
                             }
@@ -386,21 +398,49 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     }
 }
 
-template <typename R, int NA>
+template <typename R, int NA, bool ADA>
 cudaError_t launch4(const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
     size_t smem = sizeof(C) * ((size_t)t.n_keys * 9 + (size_t)t.nc4 * 9 + NA * NA * 9 + NB) +
                   sizeof(C) + sizeof(unsigned long long) * (size_t)kQChunk;
     smem = (smem + 15) & ~size_t(15);
-    cudaError_t e = cudaFuncSetAttribute(rates4_kernel<R, NA>,
+    cudaError_t e = cudaFuncSetAttribute(rates4_kernel<R, NA, ADA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long units = (long long)a.n_modes * t.N;
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (units == 0) return cudaSuccess;
-    rates4_kernel<R, NA><<<(unsigned)units, threads, smem, s>>>(t, a, ch);
+    rates4_kernel<R, NA, ADA><<<(unsigned)units, threads, smem, s>>>(t, a, ch);
     return cudaGetLastError();
 }
+
+// Dispatch over the atom count NA..HI (instantiations split across translation units so that they
+// compile in parallel; ADA selects the adaptive-σ window and Gaussian at compile time so that the
+// fixed-σ kernels carry none of its registers).
+template <typename R, bool ADA, int NA, int HI>
+cudaError_t launch4_atoms(int na, const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s) {
+    if (na == NA) return launch4<R, NA, ADA>(t, a, ch, threads, s);
+    if constexpr (NA < HI) return launch4_atoms<R, ADA, NA + 1, HI>(na, t, a, ch, threads, s);
+    else return cudaErrorInvalidValue;
+}
+
+// general-kernel launchers, one per translation unit: precision x adaptive x atoms 1-4 / 5-8
+#define FC4_GENERAL_LAUNCHER(name) \
+    cudaError_t name(int na, const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s);
+FC4_GENERAL_LAUNCHER(launch4_d_1_4)
+FC4_GENERAL_LAUNCHER(launch4_d_5_8)
+FC4_GENERAL_LAUNCHER(launch4_f_1_4)
+FC4_GENERAL_LAUNCHER(launch4_f_5_8)
+FC4_GENERAL_LAUNCHER(launch4_ad_d_1_4)
+FC4_GENERAL_LAUNCHER(launch4_ad_d_5_8)
+FC4_GENERAL_LAUNCHER(launch4_ad_f_1_4)
+FC4_GENERAL_LAUNCHER(launch4_ad_f_5_8)
+#undef FC4_GENERAL_LAUNCHER
+// tiled-path launchers (<= 2 atoms)
+cudaError_t launch4_tile_f(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
+cudaError_t launch4_tile_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
+cudaError_t launch4_tile_ad_f(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
+cudaError_t launch4_tile_ad_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
 
 }  // namespace fc4

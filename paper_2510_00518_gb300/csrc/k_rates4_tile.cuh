@@ -91,7 +91,7 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
     }
 }
 
-template <typename R, int NA>
+template <typename R, int NA, bool ADA>
 __global__ void __launch_bounds__(kTileQ, 4)
 rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
                    int mode0, const Cplx<R> *__restrict__ wall) {
@@ -155,6 +155,18 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 for (int j1 = 0; j1 < NB; ++j1) {
                     if (!((vm1 >> j1) & 1u)) continue;
                     const float b = base32[j1];
+                    if constexpr (ADA) {                         // σ per (λ'', λ'''): out-of-line rows
+                        unsigned long long kept = 0;
+                        for (int j3 = 0; j3 < NB; ++j3)
+                            if ((v3 >> j3) & 1u)
+                                kept |= (unsigned long long)window_adaptive4_row<NB>(
+                                            t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
+                                        << (NB * j3);
+                        if (kept)
+                            ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
+                                           ((unsigned long long)j1 << 40) | kept;
+                        continue;
+                    }
                     unsigned long long sure = 0, amb = 0;
 #pragma unroll
                     for (int j3 = 0; j3 < NB; ++j3)
@@ -279,7 +291,9 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         R w;
                         if constexpr (sizeof(R) == 8) {
                             const double d = delta_exact(ch, w0, t.om[m1], t.om[m2], t.om[m3]);
-                            const double g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
+                            double g;
+                            if constexpr (ADA) g = gauss_adaptive(t, a, d, m2, m3);
+                            else g = exp(-(d * d) * a.inv_sigma2) * a.gnorm;
                             w = sym4<double>(ch) * occupation_factor<double>(ch, occ[m1], occ[m2], n3) *
                                 g * invw[m0] * invw[m1] * invw[m2] * iw3;
                         } else {
@@ -289,7 +303,9 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             const float x3 = two_sum(x2, -h3, e3s);
                             const float lo = (el01 + (float)s2 * t.om32lo[m2]) - l3;
                             const float df = x3 + ((ee1 + e2s) + (e3s + lo));
-                            const float gs = __expf(-(df * df) * a.inv_sigma2_32) * a.gnorm32;
+                            float gs;
+                            if constexpr (ADA) gs = gauss_adaptive32(t, a, df, m2, m3);
+                            else gs = __expf(-(df * df) * a.inv_sigma2_32) * a.gnorm32;
                             w = sym4<float>(ch) * occupation_factor<float>(ch, n1f, occ[m2], n3) * gs *
                                 iw01 * (invw[m2] * iw3);
                         }
@@ -330,12 +346,12 @@ size_t tile_w_bytes_per_mode(const Tables &t) {
 }
 
 // Launch W (global) then the tiled kernel, over mode chunks that fit in the W buffer.
-template <typename R, int NA>
+template <typename R, int NA, bool ADA>
 cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_t s) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
     const size_t smem = tile_smem_bytes<R, NA>(t);
-    cudaError_t e = cudaFuncSetAttribute(rates4_tile_kernel<R, NA>,
+    cudaError_t e = cudaFuncSetAttribute(rates4_tile_kernel<R, NA, ADA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB);
@@ -353,7 +369,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
-        rates4_tile_kernel<R, NA><<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(
+        rates4_tile_kernel<R, NA, ADA><<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(
             t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -449,3 +449,166 @@ def test_gamma_scales_quadratically(prob2):
     g2, _, _ = prob2.with_anharmonic(phi4=p4).rates(modes)
     assert np.allclose(g2[2:], 1.7 ** 2 * g[2:], rtol=1e-13)
     assert np.array_equal(g2[:2], g[:2])
+
+
+# ------------------------------------------------------------------------------ adaptive broadening
+
+def _with_velocities(P, vel):
+    m = oracle.Modes(P.modes.omega.copy(), np.asarray(vel, np.float64).copy(), P.modes.evec, P.modes.eig)
+    return oracle.Problem(P.crystal, P.phi2, P.phi3, P.phi4, P.mesh, P.T, P.sigma, P.sigma_adaptive, m)
+
+
+@pytest.mark.parametrize("mesh", [(4, 4, 4), (2, 3, 4)])
+def test_adaptive_sigma_closed_forms(sys_clean, mesh):
+    """Adaptive width on the fcc lattice of the diamond cell, whose reciprocal vectors are
+    (2π/a)(-1,1,1), (2π/a)(1,-1,1), (2π/a)(1,1,-1) (worked out by hand from a_i = (a/2)(0,1,1) and
+    cyclic): for Δv = t x̂, each (Δv . b_k) = ±2π t/a, so σ = s (2π t / a) sqrt(Σ_k n_k^-2 / 6); for
+    Δv = t (1,1,1)/√3 each (Δv . b_k) = 2π t/(a√3).  Also σ = 0 for equal velocities, symmetry in
+    the pair and linearity in the scale s."""
+    a = 5.43
+    s = 1.7
+    P0 = oracle.Problem(*sys_clean, mesh, sigma=s, sigma_adaptive=True)
+    nm = P0.nq * P0.nb
+    t = 3.25
+    vel = np.zeros((nm, 3))
+    vel[5] = (t, 0.0, 0.0)
+    vel[6] = t * np.ones(3) / math.sqrt(3.0)
+    vel[7] = (0.4, -1.1, 2.0)
+    vel[8] = vel[7] + (0.0, 0.0, t)
+    P = _with_velocities(P0, vel)
+    inv_n2 = sum(1.0 / n ** 2 for n in mesh)
+    k = 2.0 * math.pi * t / a
+    assert P.sigma_of(5, 4) == pytest.approx(s * k * math.sqrt(inv_n2 / 6.0), rel=1e-14)
+    assert P.sigma_of(6, 4) == pytest.approx(s * k / math.sqrt(3.0) * math.sqrt(inv_n2 / 6.0), rel=1e-14)
+    assert P.sigma_of(8, 7) == pytest.approx(s * k * math.sqrt(inv_n2 / 6.0), rel=1e-14)   # Δv = t ẑ
+    assert P.sigma_of(3, 4) == 0.0 and P.sigma_of(7, 7) == 0.0
+    assert P.sigma_of(5, 6) == P.sigma_of(6, 5)
+    P2 = oracle.Problem(P.crystal, P.phi2, P.phi3, P.phi4, P.mesh, P.T, 2.0 * s, True, P.modes)
+    assert P2.sigma_of(5, 6) == pytest.approx(2.0 * P.sigma_of(5, 6), rel=1e-15)
+
+
+def test_reciprocal_vectors_definition(sys0):
+    """a_i . b_j = 2π δ_ij for the lattice of the crystal and for a skewed one."""
+    for A in (sys0[0].lattice, np.array([[3.0, 0.2, -0.1], [0.5, 4.0, 0.3], [-0.2, 0.7, 5.5]])):
+        B = oracle.reciprocal(A)
+        assert np.abs(A @ B.T - 2.0 * math.pi * np.eye(3)).max() < 1e-13
+
+
+def _brute_force_words_adaptive(P, ch, m0):
+    """Unpruned enumeration with adaptive widths: momentum closure by searching all q for the
+    Cartesian match modulo a reciprocal vector, σ from the quadratic form Δvᵀ Bᵀ diag(n^-2) B Δv
+    (a different route to the same width).  Returns (words, borderline words whose decision is
+    within 1e-9 relative of the window edge)."""
+    nb, N = P.nb, P.nq
+    B = oracle.reciprocal(P.crystal.lattice)
+    G = B.T @ np.diag(1.0 / np.asarray(P.mesh, float) ** 2) @ B
+    qs = oracle.q_cart(P.crystal.lattice, P.mesh)
+    Binv = np.linalg.inv(B)
+    w, v = P.modes.omega, P.modes.vel
+
+    cache = {}
+
+    def closure(target):
+        key = tuple(np.round(target, 9))
+        if key not in cache:
+            for k in range(N):
+                f = (qs[k] - target) @ Binv
+                if np.all(np.abs(f - np.round(f)) < 1e-9):
+                    cache[key] = k
+                    break
+        return cache[key]
+
+    def sigma(ma, mb):
+        dv = v[ma] - v[mb]
+        return P.sigma * math.sqrt(max(dv @ G @ dv, 0.0) / 6.0)
+
+    s1 = [1, -1, 1, 1, -1][ch]
+    s2 = [0, 0, 1, -1, -1][ch]
+    q0, j0 = divmod(m0, nb)
+    excl = lambda q, j: q == 0 and j < 3
+    out, border = [], set()
+    if excl(q0, j0):
+        return np.zeros(0, np.uint64), set()
+
+    def decide(word, d, sg):
+        if sg > 1e-9 and abs(abs(d) - 2.0 * sg) <= 1e-9 * max(abs(d), 2.0 * sg):
+            border.add(word)
+        if abs(sg - 1e-9) <= 1e-12:
+            border.add(word)
+        if sg > 1e-9 and abs(d) <= 2.0 * sg:      # adaptive widths at rounding-noise level are dropped
+            out.append(word)
+
+    for q1 in range(N):
+        if ch < 2:
+            q2 = closure(qs[q0] + s1 * qs[q1])
+            for j1 in range(nb):
+                for j2 in range(nb):
+                    if excl(q1, j1) or excl(q2, j2):
+                        continue
+                    m1, m2 = q1 * nb + j1, q2 * nb + j2
+                    d = w[m0] + s1 * w[m1] - w[m2]
+                    decide((q1 * nb + j1) * nb + j2, d, sigma(m1, m2))
+        else:
+            for j1 in range(nb):
+                for q2 in range(N):
+                    q3 = closure(qs[q0] + s1 * qs[q1] + s2 * qs[q2])
+                    for j2 in range(nb):
+                        for j3 in range(nb):
+                            if excl(q1, j1) or excl(q2, j2) or excl(q3, j3):
+                                continue
+                            m1, m2, m3 = q1 * nb + j1, q2 * nb + j2, q3 * nb + j3
+                            d = w[m0] + s1 * w[m1] + s2 * w[m2] - w[m3]
+                            decide((((q1 * nb + j1) * N + q2) * nb + j2) * nb + j3, d, sigma(m2, m3))
+    return np.array(out, np.uint64), border
+
+
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 2, 2), (3, 3, 3)])
+def test_enumeration_adaptive_matches_brute_force(sys0, mesh):
+    """Adaptive σ: the oracle's kept lists equal the brute-force ones up to candidates on the
+    window edge.  On the 1x1x1 and 2x2x2 meshes every q equals -q modulo a reciprocal vector, so
+    time reversal makes every group velocity vanish: σ is zero or rounding noise and nothing is
+    kept."""
+    P = oracle.Problem(*sys0, mesh, sigma=1.0, sigma_adaptive=True)
+    nm = P.nq * P.nb
+    rng = np.random.default_rng(2)
+    total = 0
+    n_pick = 4 if mesh != (3, 3, 3) else 2
+    for m0 in sorted(set(rng.integers(3, nm, size=n_pick).tolist()) | {nm - 1}):
+        for ch in range(5):
+            a = P.processes(ch, m0)
+            b, border = _brute_force_words_adaptive(P, ch, m0)
+            diff = set(a.tolist()) ^ set(b.tolist())
+            assert diff <= border, (ch, m0, len(diff))
+            total += a.size
+    if mesh != (3, 3, 3):
+        assert total == 0
+    else:
+        assert total > 0
+
+
+def test_weighted_phase_space_adaptive_brute_force(sys0):
+    """WP3- with adaptive widths: (1/N) Σ ½ (1 + n' + n'') g(Δ, σ_λ'λ'') / (ω ω' ω'') (the ½ counts
+    each unordered partner pair once), with σ by the quadratic-form route, over the brute-force
+    kept set."""
+    P = oracle.Problem(*sys0, (3, 3, 3), sigma=1.0, sigma_adaptive=True)
+    nb, N = P.nb, P.nq
+    occ = oracle.occupations(P.modes.omega, P.T)
+    w, v = P.modes.omega, P.modes.vel
+    B = oracle.reciprocal(P.crystal.lattice)
+    G = B.T @ np.diag(1.0 / np.asarray(P.mesh, float) ** 2) @ B
+    qc = oracle.q_coords(P.mesh)
+    modes = [9, 40, 100]
+    _, wp, cnt = P.rates(modes, channel_mask=2)
+    for i, m0 in enumerate(modes):
+        words, _ = _brute_force_words_adaptive(P, 1, m0)
+        assert cnt[1, i] == words.size
+        tot = 0.0
+        for wd in words.tolist():
+            q1, j1, j2 = oracle.decode3(wd, nb)
+            q2c = (qc[m0 // nb] - qc[q1]) % 3
+            m1, m2 = q1 * nb + j1, int(q2c[0] + 3 * (q2c[1] + 3 * q2c[2])) * nb + j2
+            dv = v[m1] - v[m2]
+            sg = math.sqrt(dv @ G @ dv / 6.0)
+            d = w[m0] - w[m1] - w[m2]
+            tot += 0.5 * (1 + occ[m1] + occ[m2]) * math.exp(-d * d / sg ** 2) / (sg * math.sqrt(math.pi) * w[m0] * w[m1] * w[m2])
+        assert abs(wp[1, i] - tot / N) < 1e-11 * abs(tot / N)

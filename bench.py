@@ -152,6 +152,14 @@ def clocks_stop(p, f, gpu_index):
 
 # ------------------------------------------------------------------------------ GPU arm
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per (λ, q') unit of the tiled 4ph
+# kernel, from one ncu capture of the same kernel on the 6x6x6 seed-0 crystal (279,936 units per
+# launch); key (mixed precision, channel, branches).  The bytes are the per-unit W reads, so they
+# scale with the unit count.
+TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.117304e9 + 22.25792e6) / 279936,
+                    (True, "4ph++", 6): (4.134179e9 + 35.868928e6) / 279936}
+
+
 def flops_alg(stats, info, nb):
     """Algorithmic FP32 flops of the four-phonon path per channel, counted for the factored
     contraction it performs (complex multiply-add = 8 flops, real x complex = 4):
@@ -290,8 +298,13 @@ def run_gpu(args):
         peak = 1.25                                         # FP64 (nominal GB300)
         bound_note = "FP64: nominal 1.25 TFLOP/s"
     achieved = fl / (avg[dom] * 1e-3) / 1e12
+    units = float(stats["candidates"][ch]) / (info["N"] * nb ** 3)
+    per_unit = TRAFFIC_PER_UNIT.get((prec == MIXED, dom, nb))
+    traffic = per_unit * units if per_unit else None
     roof = {"bound": "alu", "kernel": f"rates4 {dom}", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_basis": "ncu dram bytes of the same kernel on the 6x6x6 case, per (λ, q') unit, "
+                             "times this launch's units" if traffic else None,
             "launch_ms": avg[dom], "alg_flops_per_launch": fl, "peak_basis": bound_note,
             "kernel_ms": avg}
 

@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-mixed comparison")
+    p.add_argument("--no-tc", action="store_true", help="skip the tensor-core +- comparison")
     p.add_argument("--batch", action="store_true",
                    help="time the 24-crystal batch (6-24 branches) as one CUDA graph instead")
     p.add_argument("--cpu-qp", type=int, default=24, help="oracle sample: partners q' < cpu_qp")
@@ -215,6 +216,27 @@ def fp64_comparison(args, sysm, mesh, g_mixed, local):
             "gamma_rel_err_max_mixed_vs_fp64": gerr, "kappa_rel_err_mixed_vs_fp64_6x6x6": kerr}
 
 
+def tensor_core_comparison(args, eng, g_cuda):
+    """The 4ph +- channel with its cluster contraction on the tensor cores (tcgen05) beside the
+    CUDA-core run of the same step: device time of that channel's kernel (CUDA events, W shared
+    with ++ as in the step) and the largest relative Γ difference."""
+    import torch
+    eng.set_tensor_cores(True)
+    try:
+        eng.rates(args.T, args.sigma, 0b01100)                  # warm
+        gt, _, _ = eng.rates(args.T, args.sigma, 0b01100)
+        torch.cuda.synchronize()
+        ms = float(eng.timings()["4ph+-"])
+        eng.check_device()
+    finally:
+        eng.set_tensor_cores(False)
+    a, b = gt[3], g_cuda[3]
+    floor = 1e-6 * b.abs().max()
+    err = float(((a - b).abs() / torch.maximum(b.abs(), floor)).max())
+    return {"pm_ms": ms, "gamma_pm_rel_err_vs_cuda_cores": err,
+            "kernel": "rates4_tc_kernel: tcgen05.mma kind::f16, FP16 hi/lo x 3 products, FP32 accumulation"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -317,6 +339,9 @@ def run_gpu(args):
 
     if not args.no_fp64 and world == 1:
         result["fp64_gpu"] = fp64_comparison(args, sysm, mesh, g, local)
+    if prec == MIXED and world == 1 and not args.no_tc and info["n_atoms"] == 2:
+        result["tensor_cores_pm"] = tensor_core_comparison(args, eng, g)
+        result["tensor_cores_pm"]["cuda_core_pm_ms"] = avg["4ph+-"]
 
     # end to end through the C interface from host buffers
     if not args.no_e2e:

@@ -75,10 +75,12 @@ typedef struct {
 typedef struct {
     int precision;            /* fc4_precision */
     int block_threads;        /* threads per block of the 4ph kernel: 64, 96 or 128; 0 = 128 */
-    long long timeout_cycles; /* bound of device-side waits; 0 = default */
+    long long timeout_cycles; /* bound (SM clocks) of device-side waits; 0 = default (2e9, ~1 s) */
     int timing;               /* 1: record CUDA events around every kernel launch (fc4_timings) */
     int allow_unstable;       /* 1: fc4_init keeps a crystal with imaginary modes (ω set to 0 for them) */
-    int reserved[2];
+    int tensor_cores;         /* 1: 4ph +- cluster contraction on the tensor cores where available
+                                 (see fc4_set_tensor_cores); 0 = default: CUDA cores */
+    int reserved;
 } fc4_options;
 
 /* fc4_init - build a context: copy the crystal, the clusters and the mesh to the device, solve
@@ -207,6 +209,18 @@ fc4_status fc4_timings(fc4_ctx *ctx, double out[9]);
 /* fc4_set_block_threads - threads per block of the general four-phonon kernel (cells of more
  * than 2 atoms): 64, 96 or 128 (0 = 128).  A tuning knob; results do not depend on it. */
 fc4_status fc4_set_block_threads(fc4_ctx *ctx, int block_threads);
+
+/* fc4_set_tensor_cores - on = 1: in mixed precision, two-atom cells, the
+ * cluster contraction X = Σ_r P_r W_r of the 4ph +- channel runs on the tensor cores (tcgen05,
+ * FP16 hi/lo operands, three products, FP32 accumulation: FP32-level accuracy).  on = 0 (the
+ * default, faster on this workload): CUDA cores only.  Kept sets are identical either way; Γ agrees to rounding.  Other channels, the FP64
+ * path and other cells always use the CUDA cores.  Returns FC4_ERR_INVALID for other values. */
+fc4_status fc4_set_tensor_cores(fc4_ctx *ctx, int on);
+
+/* fc4_check_device - FC4_ERR_TIMEOUT if a kernel of this context gave up a bounded device-side
+ * wait since the last check (the Γ of that call were written as NaN), else FC4_OK; clears the
+ * flag.  Synchronises the device. */
+fc4_status fc4_check_device(fc4_ctx *ctx);
 
 /* fc4_info - sizes of a context: out[0..7] = n_atoms, nb, N, nc2, nc3, nc4, n_keys, precision. */
 fc4_status fc4_info(const fc4_ctx *ctx, long long out[8]);

@@ -40,7 +40,7 @@ class _IFC(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_longlong), ("timing", ctypes.c_int),
-                ("allow_unstable", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("allow_unstable", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _LIB = None
@@ -78,6 +78,8 @@ def load(build_if_missing: bool = False):
         "fc4_timings": [vp, vp],
         "fc4_rates_static": [vp, d, d, i, vp, i, vp, vp, vp, vp],
         "fc4_set_block_threads": [vp, i],
+        "fc4_set_tensor_cores": [vp, i],
+        "fc4_check_device": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -117,7 +119,8 @@ class Engine:
     ``include/fc4.h``."""
 
     def __init__(self, crystal, phi2, phi3, phi4, mesh, precision: int = FP64, block_threads: int = 0,
-                 timing: bool = False, allow_unstable: bool = False):
+                 timing: bool = False, allow_unstable: bool = False, tensor_cores: bool = False,
+                 timeout_cycles: int = 0):
         self.lib = load()
         self.mesh = tuple(int(x) for x in mesh)
         self.nq = int(np.prod(self.mesh))
@@ -156,6 +159,8 @@ class Engine:
         opt.block_threads = int(block_threads)
         opt.timing = int(bool(timing))
         opt.allow_unstable = int(bool(allow_unstable))
+        opt.tensor_cores = int(bool(tensor_cores))
+        opt.timeout_cycles = int(timeout_cycles)
         m = (ctypes.c_int * 3)(*self.mesh)
         ctx = ctypes.c_void_p()
         st = self.lib.fc4_init(ctypes.byref(c), ctypes.byref(i2), ctypes.byref(i3), ctypes.byref(i4),
@@ -186,6 +191,15 @@ class Engine:
         self._check(self.lib.fc4_info(self.ctx, _ptr(out)))
         keys = ("n_atoms", "nb", "N", "nc2", "nc3", "nc4", "n_keys", "precision")
         return dict(zip(keys, out.tolist()))
+
+    def set_tensor_cores(self, on: bool):
+        """Tensor-core cluster contraction of the 4ph +- channel (mixed precision, <= 2 atoms)."""
+        self._check(self.lib.fc4_set_tensor_cores(self.ctx, int(bool(on))))
+
+    def check_device(self):
+        """Raise FC4Error (FC4_ERR_TIMEOUT) if a bounded device-side wait expired since the last
+        check; synchronises the device."""
+        self._check(self.lib.fc4_check_device(self.ctx))
 
     def set_block_threads(self, n: int):
         """Tuning knob of the general four-phonon kernel (64, 96, 128; 0 = default)."""

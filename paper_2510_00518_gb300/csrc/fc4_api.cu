@@ -44,6 +44,9 @@ struct fc4_ctx {
     fc4::Tables t{};
     int nc2 = 0, nc3 = 0, nc4 = 0;
     int precision = FC4_FP64, block_threads = 128;
+    bool use_tc = false;                    // tensor-core contraction of the 4ph +- channel (mixed)
+    long long timeout_cycles = 0;           // bound of device-side waits (0: kernel default)
+    int *dev_err = nullptr;                 // set by a kernel whose bounded wait expired
     bool timing = false;
     bool allow_unstable = false;
     cudaEvent_t ev_a[8] = {}, ev_b[8] = {};
@@ -219,6 +222,9 @@ void prefilter(const fc4_ctx *c, double two_sigma, float *lo, float *hi) {
 // are those stated with the kernels' window test.
 void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_value) {
     a.adaptive = adaptive ? 1 : 0;
+    a.use_tc = (c->use_tc && c->precision == FC4_MIXED && fc4::tc_supported(c->t)) ? 1 : 0;
+    a.spin_limit = c->timeout_cycles;
+    a.err = c->dev_err;
     if (!adaptive) {
         const double sigma = 2.0 * kPi * sigma_value;
         a.two_sigma = 2.0 * sigma;
@@ -287,6 +293,12 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
         c->precision = opt->precision;
         c->timing = opt->timing != 0;
         c->allow_unstable = opt->allow_unstable != 0;
+        c->use_tc = opt->tensor_cores != 0;
+        if (opt->timeout_cycles < 0) {
+            delete c;
+            return fail(nullptr, FC4_ERR_INVALID, "timeout_cycles must be >= 0");
+        }
+        c->timeout_cycles = opt->timeout_cycles;
         if (opt->block_threads) {
             if (opt->block_threads % 32 || opt->block_threads < 64 || opt->block_threads > 128) {
                 delete c;
@@ -503,6 +515,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     FC4_TRY(dalloc(c, &c->vp32lo, nm));
     FC4_TRY(dalloc(c, &c->err, 1));
     FC4_TRY(cudaMemset(c->err, 0, sizeof(int)));
+    FC4_TRY(dalloc(c, &c->dev_err, 1));
+    FC4_TRY(cudaMemset(c->dev_err, 0, sizeof(int)));
     t.om = c->om;
     t.om32 = c->om32;
     t.om32lo = c->om32lo;
@@ -902,6 +916,23 @@ fc4_status fc4_set_block_threads(fc4_ctx *c, int block_threads) {
         return fail(c, FC4_ERR_INVALID, "block_threads must be 0, 64, 96 or 128");
     c->block_threads = block_threads ? block_threads : 128;
     return FC4_OK;
+}
+
+fc4_status fc4_set_tensor_cores(fc4_ctx *c, int on) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(c, FC4_ERR_INVALID, "on must be 0 or 1");
+    c->use_tc = on != 0;
+    return FC4_OK;
+}
+
+fc4_status fc4_check_device(fc4_ctx *c) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    int h = 0;
+    FC4_CUDA(c, cudaDeviceSynchronize());
+    FC4_CUDA(c, cudaMemcpy(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!h) return FC4_OK;
+    FC4_CUDA(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+    return fail(c, FC4_ERR_TIMEOUT, "a device-side wait expired (the rates of that call are NaN)");
 }
 
 fc4_status fc4_info(const fc4_ctx *c, long long out[8]) {

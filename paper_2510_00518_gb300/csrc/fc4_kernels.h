@@ -84,6 +84,9 @@ struct RateArgs {
     float ad_rlo, ad_rhi;        // prefilter: keep if |Δ32| <= ad_rlo 2σ32 - ad_e0,
     float ad_e0;                 //   reject if |Δ32| > ad_rhi 2σ32 + ad_e0, else exact FP64
     float ad_gmin;               // sure keep also needs 2σ32 > ad_gmin (σ above the noise floor)
+    int use_tc;                  // 1: tensor-core cluster contraction for 4ph +- (mixed, <= 2 atoms)
+    long long spin_limit;        // bound (SM clocks) of device-side waits; 0 = default
+    int *err;                    // device flag set by a kernel whose wait expired (may be NULL)
 };
 
 // launchers (stream-ordered; return cudaGetLastError())
@@ -91,6 +94,10 @@ struct RateArgs {
 cudaError_t launch_rates3(const Tables &t, RateArgs &a, int ch, int fp64, cudaStream_t s);
 cudaError_t launch_rates4(const Tables &t, RateArgs &a, int ch, int fp64, int threads,
                           cudaStream_t s);
+// tensor-core +- path (k_rates4_tc.cu): availability for a context, and its launch over a mode chunk
+bool tc_supported(const Tables &t);
+cudaError_t launch_rates4_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
+                             cudaStream_t s);
 // bytes of W scratch the tiled 4ph path needs per mode (0 if the general kernel is used)
 size_t rates4_wbuf_per_mode(const Tables &t, int fp64);
 cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3,

@@ -266,7 +266,7 @@ struct int5 { int a, b, c, d, e; };
 __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask, double c3, double c4,
                               const double *part_g, const double *part_wp, const long long *part_n,
                               const long long *part_items, const long long *part_ent, double *gamma,
-                              double *wp, long long *counts, unsigned long long *stats) {
+                              double *wp, long long *counts, unsigned long long *stats, const int *err) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= 5 * n_modes) return;
@@ -300,6 +300,8 @@ __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask,
     if (lane == 0) {
         const double norm = ch < 2 ? (double)N : (double)N * (double)N;
         const double cst = ch < 2 ? c3 : c4;
+        // a rate kernel whose bounded wait expired leaves incomplete partials: poison Γ
+        if (err && *err) g = __longlong_as_double(0x7ff8000000000000ll);
         gamma[(size_t)ch * n_modes + ms] = g * cst / norm;
         if (wp) wp[(size_t)ch * n_modes + ms] = p / norm;
         if (counts) counts[(size_t)ch * n_modes + ms] = n;
@@ -315,7 +317,7 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
     np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
     reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
-        gamma, wp, counts, stats);
+        gamma, wp, counts, stats, a.err);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,76 @@
+"""Tensor-core cluster contraction of the 4ph +- channel (tcgen05, mixed precision, two-atom
+cells) against the CUDA-core contraction and the FP64 oracle, and its bounded wait (needs a GB300).
+
+Both contractions feed the same window decision, so kept counts are identical; Γ agree to the
+FP32 level (1e-5) and match the oracle within the mixed-path tolerance (1e-4)."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import morse_system
+from synth.sampling import sample_q
+from tests.helpers import assert_close, make_engine, modes_of
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PM = 0b01000
+
+
+@pytest.fixture(scope="module")
+def sys0():
+    return morse_system(seed=0)
+
+
+@pytest.mark.parametrize("mesh", [(3, 3, 3), (4, 4, 4), (6, 6, 6), (5, 3, 4)])
+def test_tc_matches_cuda_cores_and_oracle(sys0, mesh):
+    """Meshes with one partial round of 128 partner points (27, 60, 64) and with two (216)."""
+    prob = oracle.Problem(*sys0, mesh)
+    e = make_engine(sys0, mesh, precision=1, prob=prob)
+    n = int(np.prod(mesh))
+    sub = sample_q(n, 3, seed=n).tolist()
+    e.set_tensor_cores(True)
+    g1, w1, c1 = (x.cpu().numpy() for x in e.rates(300.0, 0.1, PM, q_subset=sub))
+    e.set_tensor_cores(False)
+    g0, w0, c0 = (x.cpu().numpy() for x in e.rates(300.0, 0.1, PM, q_subset=sub))
+    assert c1[3].sum() > 0
+    assert np.array_equal(c1, c0)
+    assert_close(g1, g0, 1e-5, floor_frac=1e-6, what="tensor vs CUDA cores")
+    assert_close(w1, w0, 1e-5, floor_frac=1e-6, what="wp")
+    G, WP, CNT = prob.rates(modes_of(sub, 6), channel_mask=PM)
+    assert np.array_equal(c1, CNT)
+    assert_close(g1, G, 1e-4, floor_frac=1e-6, what="tensor cores vs oracle")
+
+
+def test_tc_all_channels_deterministic(sys0):
+    mesh = (4, 4, 4)
+    e = make_engine(sys0, mesh, precision=1)
+    e.set_tensor_cores(True)
+    a = e.rates(300.0, 0.1, 31)[0].cpu().numpy()
+    b = e.rates(300.0, 0.1, 31)[0].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_tc_wait_bound_expires_to_error_status(sys0):
+    """A one-clock bound on the tensor-core wait: the kernels give up before their MMAs finish,
+    flag the error, wait for the MMAs, free tensor memory and return.  Γ(+-) of that call is NaN,
+    fc4_check_device reports FC4_ERR_TIMEOUT once, and the context keeps working."""
+    from paper_2510_00518_gb300 import Engine, FC4Error, MIXED
+    mesh = (4, 4, 4)
+    prob = oracle.Problem(*sys0, mesh)
+    e = Engine(*sys0, mesh, precision=MIXED, tensor_cores=True, timeout_cycles=1)
+    e.set_modes(prob.modes.omega, prob.modes.vel, prob.modes.evec)
+    sub = [1, 2, 3]
+    g, _, _ = e.rates(300.0, 0.1, PM, q_subset=sub)
+    with pytest.raises(FC4Error) as ei:
+        e.check_device()
+    assert ei.value.status == 4
+    assert np.isnan(g[3].cpu().numpy()).all()
+    e.check_device()                                   # the flag was cleared
+    e.set_tensor_cores(False)                          # no bounded wait on this path
+    g, _, cnt = e.rates(300.0, 0.1, PM, q_subset=sub)
+    e.check_device()
+    G, _, CNT = prob.rates(modes_of(sub, 6), channel_mask=PM)
+    assert np.array_equal(cnt.cpu().numpy(), CNT)
+    assert_close(g.cpu().numpy(), G, 1e-4, floor_frac=1e-6, what="after timeout")

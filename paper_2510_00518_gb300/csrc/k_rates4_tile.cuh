@@ -27,8 +27,10 @@ __host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; 
 // summed in a fixed order, entries ordered key-major so that a warp shares one cluster range.
 constexpr int kW4Group = 8;
 
+constexpr int kW4Threads = 256;
+
 template <typename R, int NA>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kW4Threads)
 w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch, int mode0,
           Cplx<R> *wout) {
     using C = Cplx<R>;
@@ -151,6 +153,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     w2f[j] = (float)s2 * t.om32[q2 * NB + j];
                     w3f[j] = t.om32[q3 * NB + j];
                 }
+                // (j'', j''') pairs whose two partners both take part: bit NB j''' + j''
+                unsigned long long okm = 0;
+#pragma unroll
+                for (int j3 = 0; j3 < NB; ++j3)
+                    if ((v3 >> j3) & 1u) okm |= (unsigned long long)(v2 & ((1u << NB) - 1u)) << (NB * j3);
 #pragma unroll 1
                 for (int j1 = 0; j1 < NB; ++j1) {
                     if (!((vm1 >> j1) & 1u)) continue;
@@ -167,16 +174,19 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                                            ((unsigned long long)j1 << 40) | kept;
                         continue;
                     }
-                    unsigned long long sure = 0, amb = 0;
+                    float t2[NB];
+#pragma unroll
+                    for (int j2 = 0; j2 < NB; ++j2) t2[j2] = b + w2f[j2];
+                    unsigned long long le_lo = 0, le_hi = 0;    // |Δ32| <= lo32, |Δ32| <= hi32
 #pragma unroll
                     for (int j3 = 0; j3 < NB; ++j3)
 #pragma unroll
                         for (int j2 = 0; j2 < NB; ++j2) {
-                            const float ad = fabsf((b + w2f[j2]) - w3f[j3]);
-                            const bool ok = ((v3 >> j3) & (v2 >> j2) & 1u) != 0;
-                            sure |= (unsigned long long)(ok && ad <= a.lo32) << (NB * j3 + j2);
-                            amb |= (unsigned long long)(ok && ad > a.lo32 && ad <= a.hi32) << (NB * j3 + j2);
+                            const float ad = fabsf(t2[j2] - w3f[j3]);
+                            le_lo |= (unsigned long long)(ad <= a.lo32) << (NB * j3 + j2);
+                            le_hi |= (unsigned long long)(ad <= a.hi32) << (NB * j3 + j2);
                         }
+                    unsigned long long sure = le_lo & okm, amb = le_hi & ~le_lo & okm;
                     while (amb) {                                // rare: exact FP64 decision
                         const int k = __ffsll(amb) - 1;
                         amb &= amb - 1;
@@ -364,7 +374,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
         const int nm = min(chunk, a.n_modes - m);
         const long long ngrp = (t.N + kW4Group - 1) / kW4Group;
         if (!(a.w_reuse && nm == a.n_modes)) {           // W of the previous channel with the same s1
-            w4_kernel<R, NA><<<(unsigned)((long long)nm * ngrp), 128, wsmem, s>>>(t, a, ch, m,
+            w4_kernel<R, NA><<<(unsigned)((long long)nm * ngrp), kW4Threads, wsmem, s>>>(t, a, ch, m,
                                                                                   reinterpret_cast<C *>(a.wbuf));
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;

@@ -177,6 +177,14 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     float t2[NB];
 #pragma unroll
                     for (int j2 = 0; j2 < NB; ++j2) t2[j2] = b + w2f[j2];
+                    if (ch != 3) {       // ++, --: most (q'', j') have no pair near the window at all
+                        float mn = fabsf(t2[0] - w3f[0]);
+#pragma unroll
+                        for (int j3 = 0; j3 < NB; ++j3)
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2) mn = fminf(mn, fabsf(t2[j2] - w3f[j3]));
+                        if (!(mn <= a.hi32)) continue;          // nothing kept, nothing ambiguous
+                    }
                     unsigned long long le_lo = 0, le_hi = 0;    // |Δ32| <= lo32, |Δ32| <= hi32
 #pragma unroll
                     for (int j3 = 0; j3 < NB; ++j3)

@@ -15,7 +15,9 @@
 namespace fc4 {
 
 constexpr int kTileQ = 128;
-constexpr int kQPT = 4;            // partner points q'' per thread and compaction round
+// partner points q'' per thread and compaction round: 4 for the sparse ++ and -- channels (more
+// window work per round), 2 for +- (fewer registers held across its dense entry work)
+constexpr int kQPTSparse = 4, kQPTDense = 2;
 
 __host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; }
 
@@ -93,7 +95,7 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
     }
 }
 
-template <typename R, int NA, bool ADA>
+template <typename R, int NA, bool ADA, int kQPT>
 __global__ void __launch_bounds__(kTileQ, 4)
 rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
                    int mode0, const Cplx<R> *__restrict__ wall) {
@@ -350,10 +352,10 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
 }
 
 template <typename R, int NA>
-size_t tile_smem_bytes(const Tables &t) {
+size_t tile_smem_bytes(const Tables &t, int qpt = kQPTSparse) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
-    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB * kQPT;
+    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB * qpt;
     return (b + 15) & ~size_t(15);
 }
 
@@ -368,9 +370,10 @@ template <typename R, int NA, bool ADA>
 cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_t s) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
-    const size_t smem = tile_smem_bytes<R, NA>(t);
-    cudaError_t e = cudaFuncSetAttribute(rates4_tile_kernel<R, NA, ADA>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool dense = ch == 3;
+    const size_t smem = tile_smem_bytes<R, NA>(t, dense ? kQPTDense : kQPTSparse);
+    auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense> : rates4_tile_kernel<R, NA, ADA, kQPTSparse>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB);
     e = cudaFuncSetAttribute(w4_kernel<R, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
@@ -394,8 +397,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
                 continue;
             }
         }
-        rates4_tile_kernel<R, NA, ADA><<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(
-            t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
+        kern<<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -24,9 +24,11 @@ __host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; 
 
 // W[j'][r][γδ] of units (λ, q') for every partner branch j', written to global memory (layout
 // [unit][j'][r][γδ]).  One block per (λ, group of kW4Group q'): Φ contracted with e_λ and the mass
-// factor, Φ~_c[β][γδ] = Σ_α Φ_c[αβγδ] e_λ(aα) / sqrt(m), is built once in shared memory; then per
-// q' W_r = Σ_{c in r} exp(i(s1 q'.(R1 - R3) - q.R3)) Σ_β e^s1_λ'(bβ) Φ~_c[β][γδ], clusters of a key
-// summed in a fixed order, entries ordered key-major so that a warp shares one cluster range.
+// factor, Φ~_c[β][γδ] = Σ_α Φ_c[αβγδ] e_λ(aα) / sqrt(m), is built once in shared memory.  Per q' the
+// cluster phases are folded first, per key r and leg-1 atom b,
+//   Ψ_rb[β][γδ] = Σ_{c in r, b(c) = b} exp(i(s1 q'.(R1 - R3) - q.R3)) Φ~_c[β][γδ]   (fixed order),
+// and then W_r[γδ] = Σ_b Σ_β e^s1_λ'(bβ) Ψ_rb[β][γδ] for every j' (coalesced writes): the phase
+// work is shared by all partner branches.
 constexpr int kW4Group = 8;
 
 constexpr int kW4Threads = 256;
@@ -45,6 +47,7 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
     C *sPh = sPt + nc4 * 27;                                    // [nc4]
     C *sE1 = sPh + nc4;                                         // [NB][NB]  e^s1_λ'(comp) per j'
     C *se0 = sE1 + NB * NB;                                     // [NB]
+    C *sPsi = se0 + NB;                                         // [nk][NA][27]
     const int ml = blockIdx.x / ngrp, qg = blockIdx.x - ml * ngrp;
     const int m0 = a.modes[mode0 + ml];
     const int q0 = m0 / NB, j0 = m0 - q0 * NB;
@@ -76,21 +79,27 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
             sE1[k] = cconj_if(ev[(q1 * NB + comp) * NB + j1], s1 < 0);
         }
         __syncthreads();
-        C *wo = wout + ((size_t)ml * N + q1) * NB * nk * 9;
-        for (int k = threadIdx.x; k < nk * NB * 9; k += blockDim.x) {
-            const int r = k / (NB * 9), rem = k - r * (NB * 9);
-            const int j1 = rem / 9, gd = rem - j1 * 9;
+        for (int k = threadIdx.x; k < nk * NA * 27; k += blockDim.x) {
+            const int r = k / (NA * 27), rem = k - r * (NA * 27);
+            const int b = rem / 27, bgd = rem - b * 27;
             C acc = czero<C>();
-            for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c) {
-                const int b = t.c4_at[c].y;
-                const C *pt = sPt + c * 27 + gd;
-                const C *e1 = sE1 + j1 * NB + 3 * b;
-                C v = cmul(e1[0], pt[0]);
-                v = cfma(e1[1], pt[9], v);
-                v = cfma(e1[2], pt[18], v);
-                acc = cfma(sPh[c], v, acc);
-            }
-            wo[(j1 * nk + r) * 9 + gd] = acc;
+            for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c)
+                if (t.c4_at[c].y == b) acc = cfma(sPh[c], sPt[c * 27 + bgd], acc);
+            sPsi[k] = acc;
+        }
+        __syncthreads();
+        C *wo = wout + ((size_t)ml * N + q1) * NB * nk * 9;
+        for (int k = threadIdx.x; k < NB * nk * 9; k += blockDim.x) {
+            const int j1 = k / (nk * 9), rem = k - j1 * (nk * 9);
+            const int r = rem / 9, gd = rem - r * 9;
+            const C *e1 = sE1 + j1 * NB;
+            const C *ps = sPsi + r * NA * 27 + gd;
+            C acc = czero<C>();
+#pragma unroll
+            for (int b = 0; b < NA; ++b)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) acc = cfma(e1[3 * b + be], ps[b * 27 + be * 9], acc);
+            wo[k] = acc;
         }
     }
 }
@@ -375,7 +384,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
     auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense> : rates4_tile_kernel<R, NA, ADA, kQPTSparse>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB);
+    const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB + (size_t)t.n_keys * NA * 27);
     e = cudaFuncSetAttribute(w4_kernel<R, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
     if (e != cudaSuccess) return e;
     const size_t per_mode = tile_w_bytes_per_mode<R, NA>(t);

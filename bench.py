@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--once", action="store_true",
                    help="one untimed fc4_rates call (for profilers): --mesh, --precision, --mask")
     p.add_argument("--mask", type=int, default=31, help="channel mask of --once")
+    p.add_argument("--tc", action="store_true", help="--once with the tensor-core +- contraction")
     return p.parse_args()
 
 
@@ -157,8 +158,8 @@ def clocks_stop(p, f, gpu_index):
 # kernel, from one ncu capture of the same kernel on the 6x6x6 seed-0 crystal (279,936 units per
 # launch); key (mixed precision, channel, branches).  The bytes are the per-unit W reads, so they
 # scale with the unit count.
-TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.117304e9 + 22.25792e6) / 279936,
-                    (True, "4ph++", 6): (4.134179e9 + 35.868928e6) / 279936}
+TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.114713e9 + 22.477824e6) / 279936,
+                    (True, "4ph++", 6): (4.130133e9 + 33.944064e6) / 279936}
 
 
 def flops_alg(stats, info, nb):
@@ -456,9 +457,10 @@ def run_once(args):
     from paper_2510_00518_gb300 import Engine, FP64, MIXED
     sysm, mesh = workload(args, seed=0)
     eng = Engine(*sysm, mesh, precision=MIXED if args.precision == "mixed" else FP64,
-                 block_threads=args.block_threads)
+                 block_threads=args.block_threads, tensor_cores=args.tc)
     g, _, _ = eng.rates(args.T, args.sigma, args.mask)
     torch.cuda.synchronize()
+    eng.check_device()
     print("once", args.mesh, args.precision, args.mask, float(g.sum()), eng.stats())
 
 

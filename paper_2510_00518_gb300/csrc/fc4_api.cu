@@ -187,7 +187,7 @@ struct Timed {
             cudaEventRecord(c->ev_b[k], s);
             c->ev_used[k] = true;
         }
-        c->n_launches += 1;
+        if (k >= 5) c->n_launches += 1;      // rate launchers count their own kernels
     }
 };
 
@@ -225,6 +225,7 @@ void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_
     a.use_tc = (c->use_tc && c->precision == FC4_MIXED && fc4::tc_supported(c->t)) ? 1 : 0;
     a.spin_limit = c->timeout_cycles;
     a.err = c->dev_err;
+    a.n_kernels = const_cast<long long *>(&c->n_launches);
     if (!adaptive) {
         const double sigma = 2.0 * kPi * sigma_value;
         a.two_sigma = 2.0 * sigma;

@@ -87,6 +87,7 @@ struct RateArgs {
     int use_tc;                  // 1: tensor-core cluster contraction for 4ph +- (mixed, <= 2 atoms)
     long long spin_limit;        // bound (SM clocks) of device-side waits; 0 = default
     int *err;                    // device flag set by a kernel whose wait expired (may be NULL)
+    long long *n_kernels;        // host counter of kernels launched (may be NULL; never read on device)
 };
 
 // launchers (stream-ordered; return cudaGetLastError())

@@ -157,7 +157,9 @@ static cudaError_t launch3(const Tables &t, RateArgs &a, int ch, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<a.n_modes, kR3Threads, smem, s>>>(t, a, ch);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && a.n_kernels) ++*a.n_kernels;
+    return e;
 }
 
 cudaError_t launch_rates3(const Tables &t, RateArgs &a, int ch, int fp64, cudaStream_t s) {

@@ -412,7 +412,9 @@ cudaError_t launch4(const Tables &t, const RateArgs &a, int ch, int threads, cud
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (units == 0) return cudaSuccess;
     rates4_kernel<R, NA, ADA><<<(unsigned)units, threads, smem, s>>>(t, a, ch);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && a.n_kernels) ++*a.n_kernels;
+    return e;
 }
 
 // Dispatch over the atom count NA..HI (instantiations split across translation units so that they

@@ -398,17 +398,20 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
                                                                                   reinterpret_cast<C *>(a.wbuf));
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
+            if (a.n_kernels) ++*a.n_kernels;
         }
         if constexpr (sizeof(R) == 4) {
             if (ch == 3 && a.use_tc) {                  // +-: cluster contraction on the tensor cores
                 e = launch_rates4_tc(t, a, ch, m, nm, reinterpret_cast<const float2 *>(a.wbuf), s);
                 if (e != cudaSuccess) return e;
+                if (a.n_kernels) ++*a.n_kernels;
                 continue;
             }
         }
         kern<<<(unsigned)((long long)nm * t.N), kTileQ, smem, s>>>(t, a, ch, m, reinterpret_cast<const C *>(a.wbuf));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        if (a.n_kernels) ++*a.n_kernels;
     }
     return cudaSuccess;
 }

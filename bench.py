@@ -103,8 +103,8 @@ def cpu_oracle_sample(args, seed=0, qp=None, nq=None):
 
 def clocks_start():
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        out = os.environ.get("FC4_BENCH_OUT")                  # optional folder for the raw samples
+        f = open(os.path.join(out, "bench_clocks.csv") if out and os.path.isdir(out) else os.devnull, "w")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -425,8 +425,8 @@ def run_batch(args):
         c, mesh = batch_crystal(seed)
         e = Engine(c, *morse_ifcs(c, seed=seed), mesh, precision=MIXED)
         jobs.append((e, sample_q(int(np.prod(mesh)), 4, seed=seed)))
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    cache = os.path.join(out_dir, "tune_cache.json") if os.path.isdir(out_dir) else None
+    out_dir = os.environ.get("FC4_BENCH_OUT")
+    cache = os.path.join(out_dir, "tune_cache.json") if out_dir and os.path.isdir(out_dir) else None
     for e, qs in jobs:
         if e.n_atoms > 2:
             autotune(e, args.T, args.sigma, 31, qs, cache=cache)

@@ -1,32 +1,37 @@
 // k_rates4_tc.cu - four-phonon +- channel, mixed precision, two-atom cells, with the cluster
 // contraction X = Σ_r P_r^s2 W_r on the tensor cores (tcgen05).
 //
-// For a unit (λ, q') and a round of 128 partner points q'', the contraction of every (c, d) group
-// of keys is a real matrix product per partner branch j':
-//   [Xr | Xi](q'', γδ) = [Pr | s2 Pi](q'', r) . [[Wr, Wi], [-Wi, Wr]](r, γδ)
-// (rows q'' = MMA M = 128 = TMEM lanes; K = 2 x keys of the group, padded to 16; N = 32 columns of
-// which 18 hold the 9 complex γδ).  Operands are FP16 hi/lo splits (W scaled by a power of two
-// per unit so that max |W| < 1), and three products hi.hi + hi.lo + lo.hi accumulate in FP32 in
-// tensor memory: relative accuracy ~2^-21, the level of the FP32 CUDA-core contraction.  One
-// elected thread issues tcgen05.mma (kind::f16) and tcgen05.commit to an mbarrier; every thread
-// then reads its q'' row of X with tcgen05.ld.  The rows of partner points with kept processes
-// are staged in shared memory and the compacted (q'', j') entries are evaluated exactly as in the
-// CUDA-core tile kernel (Y = X e*''' per j''', V = e''.Y per kept j'', weights).
+// Persistent CTAs of 384 threads (one per SM: they hold all 512 TMEM columns) loop over units
+// (λ, q').  For a round of 128 partner points q'' the contraction of every (c, d) key group is one
+// real matrix product covering all partner branches j':
+//   [Xr | Xi](q'', j' γδ) = [Pr | s2 Pi](q'', r) . [[Wr, Wi], [-Wi, Wr]](r, j' γδ)
+// (rows q'' = MMA M = 128 = TMEM lanes; K = 2 x keys of the group, padded to 16; N = 112 columns
+// of which 108 hold the 6 x 9 complex (j', γδ)).  Operands are FP16 hi/lo splits (W scaled by a
+// power of two per unit so that max |W| < 1); the three products hi.hi + hi.lo + lo.hi accumulate
+// in FP32 in tensor memory: relative accuracy ~2^-21, the level of the FP32 CUDA-core
+// contraction.  B is built once per unit, A once per round; one thread issues tcgen05.mma
+// (kind::f16) and tcgen05.commit to an mbarrier.  The three warpgroups then share the 128 rows:
+// warpgroup g reads X of partner branches j' = g and g + 3 for its row with tcgen05.ld and
+// evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights).
 //
-// Waits on the mbarrier are bounded (fc4_options.timeout_cycles SM clocks, default 2e9); on expiry the kernel
-// sets the context's error flag (the reduction then writes NaN into Γ), waits once more (~1 s at
-// most) for its MMAs in flight, frees its tensor memory and returns.
+// Waits on the mbarrier are bounded (fc4_options.timeout_cycles SM clocks, default 2e9); on expiry
+// the kernel sets the context's error flag (the reduction then writes NaN into Γ), waits once
+// more (~1 s at most) for its MMAs in flight, writes empty partials for its remaining units, frees
+// its tensor memory and returns.
 #include "k_rates4.cuh"
 
 #include <cuda_fp16.h>
+
+#include <algorithm>
 
 namespace fc4 {
 
 namespace {
 
-constexpr int kTcRows = 128;                // q'' per round = MMA M = TMEM lanes = threads
-constexpr int kTcN = 32;                    // MMA N per (c, d) group (18 columns used)
-constexpr int kTcCols = 128;                // TMEM columns: up to 4 groups x 32
+constexpr int kTcRows = 128;                // q'' per round = MMA M = TMEM lanes
+constexpr int kTcThreads = 384;             // three warpgroups over the same 128 rows
+constexpr int kTcN = 112;                   // MMA N per (c, d) group: 6 j' x 18 columns used
+constexpr int kTcCols = 512;                // TMEM columns: 4 groups x 112, allocated as 512
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -98,11 +103,10 @@ struct TcPlan {
     int koff[4], kpad[4], nkey[4], r0[4];
 };
 
-template <int NA>
 __host__ __device__ inline TcPlan tc_plan(const Tables &t) {
     TcPlan p{};
     int o = 0;
-    for (int g = 0; g < NA * NA; ++g) {
+    for (int g = 0; g < 4; ++g) {
         p.r0[g] = t.grp_start[g];
         p.nkey[g] = t.grp_start[g + 1] - t.grp_start[g];
         p.kpad[g] = (2 * p.nkey[g] + 15) / 16 * 16;
@@ -113,109 +117,122 @@ __host__ __device__ inline TcPlan tc_plan(const Tables &t) {
     return p;
 }
 
-// shared memory: A hi | A lo (128 x kt halves each) | B hi | B lo (32 x kt) | X rows | entries
-template <int NA>
+// shared memory: A hi | A lo (128 x kt halves each) | B hi | B lo (112 x kt halves each)
 __host__ __device__ inline size_t tc_smem_bytes(const Tables &t) {
-    const TcPlan p = tc_plan<NA>(t);
-    return (size_t)2 * kTcRows * p.kt * 2 + (size_t)2 * kTcN * p.kt * 2 +
-           (size_t)kTcRows * NA * NA * 9 * sizeof(float2) + (size_t)kTcRows * sizeof(unsigned long long) + 128;
+    const TcPlan p = tc_plan(t);
+    return (size_t)2 * kTcRows * p.kt * 2 + (size_t)2 * kTcN * p.kt * 2 + 128;
 }
 
-template <int NA, bool ADA>
-__global__ void __launch_bounds__(kTcRows, 2)
+template <bool ADA>
+__global__ void __launch_bounds__(kTcThreads, 1)
 rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch, int mode0,
-                 const float2 *__restrict__ wall) {
-    constexpr int NB = 3 * NA;
-    constexpr int NG = NA * NA;
+                 int n_units, const float2 *__restrict__ wall) {
+    constexpr int NA = 2, NB = 6, NG = 4;
     const int s1 = (ch == 4) ? -1 : 1;
     const int s2 = (ch == 2) ? 1 : -1;
     const int N = t.N, nk = t.n_keys;
-    const TcPlan pl = tc_plan<NA>(t);
+    const TcPlan pl = tc_plan(t);
 
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char *sA = tc_smem;                                            // hi, then lo at + 256 kt
-    unsigned char *sB = sA + (size_t)2 * kTcRows * pl.kt * 2;            // hi, then lo at + 64 kt
-    float2 *sX = reinterpret_cast<float2 *>(sB + (size_t)2 * kTcN * pl.kt * 2);   // [128][NG][9]
-    unsigned long long *sE = reinterpret_cast<unsigned long long *>(sX + kTcRows * NG * 9);
+    unsigned char *sA = tc_smem;                                         // hi, then lo at + 256 kt
+    unsigned char *sB = sA + (size_t)2 * kTcRows * pl.kt * 2;            // hi, then lo at + 224 kt
     const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + 256u * pl.kt;
-    const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + 64u * pl.kt;
+    const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + 224u * pl.kt;
     __shared__ __align__(8) unsigned long long s_mbar;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_scan[32];
     __shared__ double s_red[2 * 32];
     __shared__ long long s_redn[3 * 32];
-    __shared__ float s_wmax[4];
+    __shared__ float s_wmax[kTcThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int unit = blockIdx.x;
-    const int ml = unit / N, q1 = unit - ml * N;
-    const int ms = mode0 + ml;
-    const int m0 = a.modes[ms];
-    const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+    const int row = tid & (kTcRows - 1), wg = tid >> 7;         // TMEM lane = row; warpgroup
+    constexpr int nj = 2;                                       // partner branches per warpgroup: g, g + 3
     const float2 *ev = t.ev32;
     const float *occ = t.occ32;
     const float *invw = t.invw32;
     const long long spins = a.spin_limit > 0 ? a.spin_limit : 2000000000ll;   // ~1 s
     const uint32_t mbar = smem_u32(&s_mbar);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
-    Acc<float> acc_g, acc_wp;
-    long long acc_n = 0, acc_items = 0, acc_ent = 0;
-    const unsigned vm1 = t.vmask[q1];
-    const bool active = !(q0 == 0 && j0 < 3) && vm1;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&s_tmem)), "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // B padding (rows 108..111, K columns beyond 2 x keys) stays zero for the whole kernel
+    for (int k = tid; k < 2 * kTcN * pl.kt / 2; k += kTcThreads) reinterpret_cast<uint32_t *>(sB)[k] = 0u;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    uint32_t phase = 0;
+    bool dead = false;
+    int unit = blockIdx.x;
 
-    if (active) {                                   // uniform across the block
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar));
-            asm volatile("fence.mbarrier_init.release.cluster;");
-        }
-        if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                         :: "r"(smem_u32(&s_tmem)), "r"(kTcCols));
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-        }
-        const float2 *wsrc = wall + (size_t)unit * (NB * nk * 9);
-        // per-unit power-of-two scale of W: max |W| * 2^-E in [0.5, 1)
-        float mx = 0.0f;
-        for (int k = tid; k < NB * nk * 9; k += kTcRows) {
-            const float2 w = wsrc[k];
-            mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
-        }
+    for (; unit < n_units && !dead; unit += gridDim.x) {
+        const int ml = unit / N, q1 = unit - ml * N;
+        const int ms = mode0 + ml;
+        const int m0 = a.modes[ms];
+        const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+        Acc<float> acc_g, acc_wp;
+        long long acc_n = 0, acc_items = 0, acc_ent = 0;
+        const unsigned vm1 = t.vmask[q1];
+        if (!(q0 == 0 && j0 < 3) && vm1) {                       // uniform across the block
+            const float2 *wsrc = wall + (size_t)unit * (NB * nk * 9);
+            float mx = 0.0f;
+            for (int k = tid; k < NB * nk * 9; k += kTcThreads) {
+                const float2 w = wsrc[k];
+                mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-        if ((tid & 31) == 0) s_wmax[warp] = mx;
-        // B padding (rows 18..31 and K columns beyond 2 x keys) is zero for the whole kernel
-        for (int k = tid; k < 2 * kTcN * pl.kt / 2; k += kTcRows)
-            reinterpret_cast<uint32_t *>(sB)[k] = 0u;
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t tmem = s_tmem;
-        int e_w = 0;
-        {
-            const float m = fmaxf(fmaxf(s_wmax[0], s_wmax[1]), fmaxf(s_wmax[2], s_wmax[3]));
-            if (m > 0.0f) frexpf(m, &e_w);
-        }
-        const float wscale = ldexpf(1.0f, -e_w), xscale = ldexpf(1.0f, e_w);
-
-        const int4 c0 = t.qc[q0], c1 = t.qc[q1];
-        const int b0 = c0.x + s1 * c1.x, b1 = c0.y + s1 * c1.y, b2 = c0.z + s1 * c1.z;
-        const double w0 = t.om[m0];
-        const float w0f = t.om32[m0];
-        float base32[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) base32[j] = w0f + (float)s1 * t.om32[q1 * NB + j];
-        uint32_t phase = 0;
-        bool dead = false;
-
-        for (int qb = 0; qb < N && !dead; qb += kTcRows) {
-            const int q2 = qb + tid;
-            const bool valid = q2 < N;
-            int q3 = 0;
-            // A row of this thread's q'': [Pr | s2 Pi] per group, FP16 hi / lo
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+            if ((tid & 31) == 0) s_wmax[warp] = mx;
+            __syncthreads();                                     // also: the previous unit is done
+            int e_w = 0;
             {
-                const float2 *Prow = t.P4_32 + (size_t)(valid ? q2 : 0) * nk;
+                float m = 0.0f;
+                for (int w = 0; w < kTcThreads / 32; ++w) m = fmaxf(m, s_wmax[w]);
+                if (m > 0.0f) frexpf(m, &e_w);
+            }
+            const float wscale = ldexpf(1.0f, -e_w), xscale = ldexpf(1.0f, e_w);
+            // B of the unit: row n = 18 j' + 2 γδ + (0 re, 1 im) of every group, FP16 hi / lo
+            for (int k = tid; k < NB * nk * 9; k += kTcThreads) {
+                const int j1 = k / (nk * 9), rem = k - j1 * (nk * 9);
+                const int r = rem / 9, gd = rem - r * 9;
+                int g = 0;
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
+                for (int gg = 1; gg < NG; ++gg) g += (r >= pl.r0[gg]);
+                const int kr = r - pl.r0[g];
+                const float2 w = wsrc[k];
+                const float wr = w.x * wscale, wi = w.y * wscale;
+                const float val[4] = {wr, -wi, wi, wr};        // (re row: k, K + k), (im row: k, K + k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int n = 18 * j1 + 2 * gd + (u >> 1);
+                    const int kk = pl.koff[g] + kr + ((u & 1) ? pl.nkey[g] : 0);
+                    __half h, l;
+                    split_f16(val[u], h, l);
+                    const uint32_t off = tile_off(n, kk, kTcN);
+                    *reinterpret_cast<__half *>(sB + off) = h;
+                    *reinterpret_cast<__half *>(sB + 224u * pl.kt + off) = l;
+                }
+            }
+
+            const int4 c0 = t.qc[q0], c1 = t.qc[q1];
+            const int b0 = c0.x + s1 * c1.x, b1 = c0.y + s1 * c1.y, b2 = c0.z + s1 * c1.z;
+            const double w0 = t.om[m0];
+            const float w0f = t.om32[m0];
+
+            for (int qb = 0; qb < N && !dead; qb += kTcRows) {
+                const int q2 = qb + row;
+                const bool valid = q2 < N;
+                // A: row `row`, the warpgroup's groups (0 | 1, 2 | 3: its share of the row), FP16 hi / lo
+                const float2 *Prow = t.P4_32 + (size_t)(valid ? q2 : 0) * nk;
+                for (int g = (wg == 0 ? 0 : wg == 1 ? 1 : 3); g <= (wg == 0 ? 0 : wg == 1 ? 2 : 3); ++g) {
                     for (int k = 0; k < pl.kpad[g]; k += 2) {
                         float v[2];
 #pragma unroll
@@ -231,102 +248,81 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                         __half h0, l0, h1, l1;
                         split_f16(v[0], h0, l0);
                         split_f16(v[1], h1, l1);
-                        const uint32_t off = tile_off(tid, pl.koff[g] + k, kTcRows);
+                        const uint32_t off = tile_off(row, pl.koff[g] + k, kTcRows);
                         *reinterpret_cast<__half2 *>(sA + off) = __halves2half2(h0, h1);
                         *reinterpret_cast<__half2 *>(sA + 256u * pl.kt + off) = __halves2half2(l0, l1);
                     }
                 }
-            }
-            // window: kept masks of this q'' for every partner branch j' (bit NB j''' + j'')
-            unsigned long long keep[NB];
+                // window of this row for the warpgroup's partner branches: bit NB j3 + j2 set iff kept
+                unsigned long long keep[2] = {0ull, 0ull};
+                int q3 = 0;
+                if (valid) {
+                    const int4 c2 = t.qc[q2];
+                    q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z, t.mesh[0], t.mesh[1], t.mesh[2]);
+                    const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+                    float w2f[NB], w3f[NB];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) keep[j] = 0ull;
-            if (valid) {
-                const int4 c2 = t.qc[q2];
-                q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z, t.mesh[0], t.mesh[1], t.mesh[2]);
-                const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
-                float w2f[NB], w3f[NB];
-#pragma unroll
-                for (int j = 0; j < NB; ++j) {
-                    w2f[j] = (float)s2 * t.om32[q2 * NB + j];
-                    w3f[j] = t.om32[q3 * NB + j];
-                }
-#pragma unroll
-                for (int j1 = 0; j1 < NB; ++j1) {
-                    if (!((vm1 >> j1) & 1u)) continue;
-                    const float b = base32[j1];
-                    if constexpr (ADA) {
-                        unsigned long long kept = 0;
-                        for (int j3 = 0; j3 < NB; ++j3)
-                            if ((v3 >> j3) & 1u)
-                                kept |= (unsigned long long)window_adaptive4_row<NB>(
-                                            t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
-                                        << (NB * j3);
-                        keep[j1] = kept;
-                    } else {
-                        unsigned long long sure = 0, amb = 0;
-#pragma unroll
-                        for (int j3 = 0; j3 < NB; ++j3)
-#pragma unroll
-                            for (int j2 = 0; j2 < NB; ++j2) {
-                                const float ad = fabsf((b + w2f[j2]) - w3f[j3]);
-                                const bool ok = ((v3 >> j3) & (v2 >> j2) & 1u) != 0;
-                                sure |= (unsigned long long)(ok && ad <= a.lo32) << (NB * j3 + j2);
-                                amb |= (unsigned long long)(ok && ad > a.lo32 && ad <= a.hi32) << (NB * j3 + j2);
-                            }
-                        while (amb) {
-                            const int k = __ffsll(amb) - 1;
-                            amb &= amb - 1;
-                            const int j3 = k / NB, j2 = k - j3 * NB;
-                            if (window_exact4(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], t.om[q3 * NB + j3],
-                                              a.two_sigma))
-                                sure |= 1ull << k;
-                        }
-                        keep[j1] = sure;
+                    for (int j = 0; j < NB; ++j) {
+                        w2f[j] = (float)s2 * t.om32[q2 * NB + j];
+                        w3f[j] = t.om32[q3 * NB + j];
                     }
-                }
-            }
-
-            for (int j1 = 0; j1 < NB && !dead; ++j1) {
-                if (!((vm1 >> j1) & 1u)) continue;
-                if (!__syncthreads_or(keep[j1] != 0ull)) continue;      // no entry in this round
-                // B of (unit, j'): rows 2γδ (re) and 2γδ + 1 (im) of every group, FP16 hi / lo
-                {
-                    const float2 *wj = wsrc + (size_t)j1 * nk * 9;
-                    for (int k = tid; k < nk * 9; k += kTcRows) {
-                        const int r = k / 9, gd = k - r * 9;
-                        int g = 0;
+                    unsigned long long okm = 0;
 #pragma unroll
-                        for (int gg = 1; gg < NG; ++gg) g += (r >= pl.r0[gg]);
-                        const int kr = r - pl.r0[g];
-                        const float2 w = wj[k];
-                        const float wr = w.x * wscale, wi = w.y * wscale;
-                        const float val[4] = {wr, -wi, wi, wr};    // (re row: k, K + k), (im row: k, K + k)
+                    for (int j3 = 0; j3 < NB; ++j3)
+                        if ((v3 >> j3) & 1u) okm |= (unsigned long long)(v2 & ((1u << NB) - 1u)) << (NB * j3);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int n = 2 * gd + (u >> 1);
-                            const int kk = pl.koff[g] + kr + ((u & 1) ? pl.nkey[g] : 0);
-                            __half h, l;
-                            split_f16(val[u], h, l);
-                            const uint32_t off = tile_off(n, kk, kTcN);
-                            *reinterpret_cast<__half *>(sB + off) = h;
-                            *reinterpret_cast<__half *>(sB + 64u * pl.kt + off) = l;
+                    for (int jj = 0; jj < nj; ++jj) {
+                        const int j1 = wg + 3 * jj;
+                        if (!((vm1 >> j1) & 1u)) continue;
+                        const float b = w0f + (float)s1 * t.om32[q1 * NB + j1];
+                        if constexpr (ADA) {
+                            unsigned long long kept = 0;
+                            for (int j3 = 0; j3 < NB; ++j3)
+                                if ((v3 >> j3) & 1u)
+                                    kept |= (unsigned long long)window_adaptive4_row<NB>(
+                                                t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
+                                            << (NB * j3);
+                            keep[jj] = kept;
+                        } else {
+                            float t2[NB];
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2) t2[j2] = b + w2f[j2];
+                            unsigned long long le_lo = 0, le_hi = 0;
+#pragma unroll
+                            for (int j3 = 0; j3 < NB; ++j3)
+#pragma unroll
+                                for (int j2 = 0; j2 < NB; ++j2) {
+                                    const float ad = fabsf(t2[j2] - w3f[j3]);
+                                    le_lo |= (unsigned long long)(ad <= a.lo32) << (NB * j3 + j2);
+                                    le_hi |= (unsigned long long)(ad <= a.hi32) << (NB * j3 + j2);
+                                }
+                            unsigned long long sure = le_lo & okm, amb = le_hi & ~le_lo & okm;
+                            while (amb) {
+                                const int k = __ffsll(amb) - 1;
+                                amb &= amb - 1;
+                                const int j3 = k / NB, j2 = k - j3 * NB;
+                                if (window_exact4(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2],
+                                                  t.om[q3 * NB + j3], a.two_sigma))
+                                    sure |= 1ull << k;
+                            }
+                            keep[jj] = sure;
                         }
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
+                const int any = __syncthreads_or((keep[0] | keep[1]) != 0ull);
+                if (!any) continue;                              // no entry in this round
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        for (int pz = 0; pz < 3; ++pz) {                 // hi.hi, hi.lo, lo.hi
+                        for (int pz = 0; pz < 3; ++pz) {         // hi.hi, hi.lo, lo.hi
                             const uint32_t ab = (pz == 2 ? a_lo : a_hi) + 256u * pl.koff[g];
-                            const uint32_t bb = (pz == 1 ? b_lo : b_hi) + 64u * pl.koff[g];
+                            const uint32_t bb = (pz == 1 ? b_lo : b_hi) + 224u * pl.koff[g];
                             for (int s = 0; s < pl.kpad[g] / 16; ++s)
                                 mma_f16(tmem + (uint32_t)(kTcN * g), smem_desc(ab + 4096u * s, 2048u, 128u),
-                                        smem_desc(bb + 1024u * s, 512u, 128u), (pz > 0 || s > 0) ? 1u : 0u);
+                                        smem_desc(bb + 3584u * s, 1792u, 128u), (pz > 0 || s > 0) ? 1u : 0u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -334,47 +330,31 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                 }
                 const bool ok = mbar_wait(mbar, phase, spins);
                 phase ^= 1u;
-                if (__syncthreads_or(!ok)) {                             // the MMAs did not complete
+                if (__syncthreads_or(!ok)) {                     // the MMAs did not complete
                     if (tid == 0 && a.err) atomicExch(a.err, 1);
                     mbar_wait(mbar, phase ^ 1u, 2000000000ll);   // let the MMAs in flight finish
                     dead = true;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                // this thread's row of X (all groups), scaled back
-                float xr[NG][18];
+                const int iq2 = q2, iq3 = q3;
+                for (int jj = 0; jj < nj; ++jj) {
+                    const int j1 = wg + 3 * jj;
+                    // this row's X for partner branch j1 (warp-collective loads)
+                    float xr[NG][18];
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    if (pl.nkey[g] == 0) {
+                    for (int g = 0; g < NG; ++g) {
+                        if (pl.nkey[g] == 0) {
 #pragma unroll
-                        for (int k = 0; k < 18; ++k) xr[g][k] = 0.0f;
-                    } else {
-                        tmem_ld18(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kTcN * g), xr[g]);
+                            for (int k = 0; k < 18; ++k) xr[g][k] = 0.0f;
+                        } else {
+                            tmem_ld18(tmem + lane_base + (uint32_t)(kTcN * g + 18 * j1), xr[g]);
+                        }
                     }
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                // compact this j' 's entries; stage their X rows
-                const unsigned long long mk = keep[j1];
-                int total;
-                const int off = block_exclusive_scan(mk != 0ull ? 1 : 0, s_scan, &total);
-                if (mk) {
-                    sE[off] = ((unsigned long long)tid << 48) | mk;
-                    float2 *dst = sX + (size_t)off * NG * 9;
-#pragma unroll
-                    for (int g = 0; g < NG; ++g)
-#pragma unroll
-                        for (int k = 0; k < 9; ++k)
-                            dst[g * 9 + k] = make_float2(xr[g][2 * k] * xscale, xr[g][2 * k + 1] * xscale);
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
-                for (int it = tid; it < total; it += kTcRows) {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    const unsigned long long e = keep[jj];
+                    if (!e) continue;
                     ++acc_ent;
-                    const unsigned long long e = sE[it];
-                    const int iq2 = qb + (int)(e >> 48);
-                    const int4 cc2 = t.qc[iq2];
-                    const int iq3 = q_index_near(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
-                                                 t.mesh[0], t.mesh[1], t.mesh[2]);
                     const int m1 = q1 * NB + j1;
                     float ee1;
                     const float ex1 = two_sum(t.om32[m0], (float)s1 * t.om32[m1], ee1);
@@ -382,13 +362,13 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                     const float iw01 = invw[m0] * invw[m1];
                     const float n1f = occ[m1];
                     float2 X[NA][NA][9];
-                    const float2 *src = sX + (size_t)it * NG * 9;
 #pragma unroll
                     for (int c = 0; c < NA; ++c)
 #pragma unroll
                         for (int d = 0; d < NA; ++d)
 #pragma unroll
-                            for (int k = 0; k < 9; ++k) X[c][d][k] = src[(c * NA + d) * 9 + k];
+                            for (int k = 0; k < 9; ++k)
+                                X[c][d][k] = make_float2(xr[c * NA + d][2 * k] * xscale, xr[c * NA + d][2 * k + 1] * xscale);
 #pragma unroll 1
                     for (int j3 = 0; j3 < NB; ++j3) {
                         unsigned m = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);
@@ -440,49 +420,70 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                         }
                     }
                 }
-                __syncthreads();                                         // sX / sE reused next
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();                                 // A and TMEM are reused next round
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
+        double sums[2] = {acc_g.value(), acc_wp.value()};
+        long long cnts[3] = {acc_n, acc_items, acc_ent};
+        block_sum_multi<2, 3>(sums, cnts, s_red, s_redn);
+        if (tid == 0) {
+            const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
+            a.part_g[o] = sums[0];
+            a.part_wp[o] = sums[1];
+            a.part_n[o] = cnts[0];
+            a.part_items[o] = cnts[1];
+            a.part_ent[o] = cnts[2];
+        }
     }
-    double sums[2] = {acc_g.value(), acc_wp.value()};
-    long long cnts[3] = {acc_n, acc_items, acc_ent};
-    block_sum_multi<2, 3>(sums, cnts, s_red, s_redn);
-    if (threadIdx.x == 0) {
-        const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
-        a.part_g[o] = sums[0];
-        a.part_wp[o] = sums[1];
-        a.part_n[o] = cnts[0];
-        a.part_items[o] = cnts[1];
-        a.part_ent[o] = cnts[2];
+    if (dead && tid == 0) {
+        // the abandoned units still get partial slots for the reduction to read (their Γ is
+        // poisoned through the error flag)
+        for (unit -= gridDim.x; unit < n_units; unit += gridDim.x) {
+            const int ml = unit / N, q1 = unit - ml * N;
+            const size_t o = ((size_t)ch * a.n_modes + mode0 + ml) * N + q1;
+            a.part_g[o] = 0.0;
+            a.part_wp[o] = 0.0;
+            a.part_n[o] = 0;
+            a.part_items[o] = 0;
+            a.part_ent[o] = 0;
+        }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
 }
 
-template <int NA, bool ADA>
+template <bool ADA>
 static cudaError_t launch_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
                              cudaStream_t s) {
-    const size_t smem = tc_smem_bytes<NA>(t);
-    cudaError_t e = cudaFuncSetAttribute(rates4_tc_kernel<NA, ADA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = tc_smem_bytes(t);
+    cudaError_t e = cudaFuncSetAttribute(rates4_tc_kernel<ADA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    rates4_tc_kernel<NA, ADA><<<(unsigned)((long long)nm * t.N), kTcRows, smem, s>>>(t, a, ch, mode0, w);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long units = (long long)nm * t.N;
+    if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const int grid = (int)std::min<long long>(units, (long long)std::max(sms, 1));   // one CTA per SM
+    if (grid == 0) return cudaSuccess;
+    rates4_tc_kernel<ADA><<<grid, kTcThreads, smem, s>>>(t, a, ch, mode0, (int)units, w);
     return cudaGetLastError();
 }
 
-// Used for two-atom cells whose operands fit in shared memory next to a second block of the same
-// size on the SM (other cells keep the CUDA-core kernels).
+// Used for two-atom cells whose operands fit in shared memory (other cells keep the CUDA-core
+// kernels).
 bool tc_supported(const Tables &t) {
-    return t.n_atoms == 2 && tc_smem_bytes<2>(t) <= 110 * 1024;
+    return t.n_atoms == 2 && tc_smem_bytes(t) <= 200 * 1024;
 }
 
 cudaError_t launch_rates4_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
                              cudaStream_t s) {
-    const bool ad = a.adaptive != 0;
     if (t.n_atoms != 2) return cudaErrorInvalidValue;
-    return ad ? launch_tc<2, true>(t, a, ch, mode0, nm, w, s) : launch_tc<2, false>(t, a, ch, mode0, nm, w, s);
+    return a.adaptive ? launch_tc<true>(t, a, ch, mode0, nm, w, s) : launch_tc<false>(t, a, ch, mode0, nm, w, s);
 }
 
 }  // namespace fc4

@@ -2,6 +2,7 @@
 // layout of the clusters (keys, phase indices, mass factors), device tables, and the
 // stream-ordered launch sequence of each call.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -55,6 +56,8 @@ struct fc4_ctx {
     double volume = 0.0;
     std::vector<void *> owned;
     std::vector<int> perm4;                 // device cluster slot -> input cluster index
+    std::vector<int> swap12, swap23;        // input cluster -> the cluster with legs 1,2 (2,3) swapped
+    bool sym12 = false, sym23 = false;      // Φ4 invariant under those swaps (triangular domains)
     std::vector<double> om_host;            // current ω (for the prefilter bound)
     double vmax = 0.0;                      // max |v| over modes (adaptive prefilter bound)
     // writable views of the tables
@@ -201,6 +204,34 @@ fc4_status ensure_occupations(fc4_ctx *c, double T, cudaStream_t s) {
     return FC4_OK;
 }
 
+// Leg-swap invariance of Φ4 (input cluster order): every cluster has its partner with legs 1, 2
+// (resp. 2, 3) exchanged, with the correspondingly transposed tensor, to 1e-12 of max |Φ4|.  The
+// triangular domains of the 4ph sums are used only then (a single perturbed entry, as in a
+// finite-difference check of the gradient, falls back to the rectangular sum).
+void check_sym4(fc4_ctx *c, const double *phi) {
+    double mx = 0.0;
+    for (size_t k = 0; k < 81 * (size_t)c->nc4; ++k) mx = std::max(mx, std::fabs(phi[k]));
+    const double tol = 1e-12 * mx;
+    auto ok = [&](const std::vector<int> &sw, bool twelve) {
+        for (int i = 0; i < c->nc4; ++i) {
+            const int j = sw[i];
+            if (j < 0) return false;
+            const double *p = phi + 81 * (size_t)i, *q = phi + 81 * (size_t)j;
+            for (int al = 0; al < 3; ++al)
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y)
+                        for (int z = 0; z < 3; ++z) {
+                            const double v = p[((al * 3 + x) * 3 + y) * 3 + z];
+                            const double w = twelve ? q[((al * 3 + y) * 3 + x) * 3 + z] : q[((al * 3 + x) * 3 + z) * 3 + y];
+                            if (std::fabs(v - w) > tol) return false;
+                        }
+        }
+        return true;
+    };
+    c->sym12 = ok(c->swap12, true);
+    c->sym23 = ok(c->swap23, false);
+}
+
 // Prefilter thresholds: |Δ32 - Δ64| <= 13 u ω_max (u = 2^-24; three roundings of the inputs'
 // partial sums plus four input roundings); margin 32 u ω_max, doubled to cover the rounding of
 // the thresholds themselves.
@@ -226,6 +257,7 @@ void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_
     a.spin_limit = c->timeout_cycles;
     a.err = c->dev_err;
     a.n_kernels = const_cast<long long *>(&c->n_launches);
+    a.tri = (c->sym23 ? 1 : 0) | (c->sym12 && !adaptive ? 2 : 0);
     if (!adaptive) {
         const double sigma = 2.0 * kPi * sigma_value;
         a.two_sigma = 2.0 * sigma;
@@ -421,6 +453,30 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     // fourth order: key = (leg-2 atom, leg-3 atom, R2 - R3); keys ordered by group, clusters by key
     c->nc4 = phi4 ? phi4->n_clusters : 0;
     t.nc4 = c->nc4;
+    if (c->nc4) {   // leg-swap partners of every cluster (for the triangular 4ph domains)
+        using CK = std::array<int, 13>;
+        std::map<CK, int> id;
+        auto key = [&](int i, int l1, int l2, int l3) {
+            const int *a = phi4->atoms + 4 * i, *R = phi4->cells + 9 * i;
+            const int l[3] = {l1, l2, l3};
+            CK k{};
+            k[0] = a[0];
+            for (int m = 0; m < 3; ++m) {
+                k[1 + m] = a[1 + l[m]];
+                for (int x = 0; x < 3; ++x) k[4 + 3 * m + x] = R[3 * l[m] + x];
+            }
+            return k;
+        };
+        for (int i = 0; i < c->nc4; ++i) id.emplace(key(i, 0, 1, 2), i);
+        c->swap12.assign(c->nc4, -1);
+        c->swap23.assign(c->nc4, -1);
+        for (int i = 0; i < c->nc4; ++i) {
+            auto f12 = id.find(key(i, 1, 0, 2)), f23 = id.find(key(i, 0, 2, 1));
+            if (f12 != id.end()) c->swap12[i] = f12->second;
+            if (f23 != id.end()) c->swap23[i] = f23->second;
+        }
+        check_sym4(c, phi4->phi);
+    }
     {
         using Key = std::tuple<int, int, int, int>;   // group, dR
         std::map<Key, int> key_id;
@@ -868,6 +924,7 @@ fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *p
     if (phi3 && c->nc3)
         FC4_CUDA(c, cudaMemcpy(c->phi3, phi3, 27 * (size_t)c->nc3 * sizeof(double), cudaMemcpyHostToDevice));
     if (phi4 && c->nc4) {
+        check_sym4(c, phi4);
         std::vector<double> ph(81 * (size_t)c->nc4);
         std::vector<float> ph32(81 * (size_t)c->nc4);
         for (int s = 0; s < c->nc4; ++s)

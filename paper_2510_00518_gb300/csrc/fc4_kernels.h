@@ -88,6 +88,8 @@ struct RateArgs {
     long long spin_limit;        // bound (SM clocks) of device-side waits; 0 = default
     int *err;                    // device flag set by a kernel whose wait expired (may be NULL)
     long long *n_kernels;        // host counter of kernels launched (may be NULL; never read on device)
+    int tri;                     // triangular 4ph domain allowed: bit 0 +- (Φ4 symmetric in legs 2, 3),
+                                 // bit 1 ++ and -- (legs 1, 2; fixed σ only)
 };
 
 // launchers (stream-ordered; return cudaGetLastError())

@@ -164,15 +164,41 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     w2f[j] = (float)s2 * t.om32[q2 * NB + j];
                     w3f[j] = t.om32[q3 * NB + j];
                 }
+                // Triangular domain (partner-swap symmetry of the summand): +- is symmetric under
+                // (λ'', λ''') (q'' <-> q''' at fixed q'), ++ and -- under (λ', λ'') (q' <-> q'') when σ
+                // is fixed.  One representative of each pair is evaluated with weight 2; a self-paired
+                // point keeps the ordered half of its branch pairs.  The exact window test and the
+                // summand are swap-symmetric, so counts and Γ equal those of the rectangular sum.
+                int tri = 0;           // 0: weight 1; 1: weight 2; 2: +- with q'' = q'''; 3: ++/-- with q'' = q'
+                if (ch == 3 && (a.tri & 1)) {
+                    if (q2 > q3) continue;                       // the swap of (q3, q2)
+                    tri = q2 < q3 ? 1 : 2;
+                } else if (ch != 3 && (a.tri & 2)) {
+                    if (q2 < q1) continue;                       // the swap of (q2, q1)
+                    tri = q2 > q1 ? 1 : 3;
+                }
                 // (j'', j''') pairs whose two partners both take part: bit NB j''' + j''
                 unsigned long long okm = 0;
 #pragma unroll
                 for (int j3 = 0; j3 < NB; ++j3)
-                    if ((v3 >> j3) & 1u) okm |= (unsigned long long)(v2 & ((1u << NB) - 1u)) << (NB * j3);
+                    if ((v3 >> j3) & 1u) {
+                        unsigned row = v2 & ((1u << NB) - 1u);
+                        if (tri == 2) row &= (2u << j3) - 1u;    // j'' <= j'''
+                        okm |= (unsigned long long)row << (NB * j3);
+                    }
 #pragma unroll 1
                 for (int j1 = 0; j1 < NB; ++j1) {
                     if (!((vm1 >> j1) & 1u)) continue;
                     const float b = base32[j1];
+                    unsigned long long okj = okm;                // tri 3: j'' >= j'
+                    if (tri == 3) {
+                        const unsigned long long row = (unsigned long long)(((1u << NB) - 1u) & ~((1u << j1) - 1u));
+                        unsigned long long cm = 0;
+#pragma unroll
+                        for (int j3 = 0; j3 < NB; ++j3) cm |= row << (NB * j3);
+                        okj &= cm;
+                    }
+                    const unsigned long long tri_bits = (unsigned long long)tri << 36;
                     if constexpr (ADA) {                         // σ per (λ'', λ'''): out-of-line rows
                         unsigned long long kept = 0;
                         for (int j3 = 0; j3 < NB; ++j3)
@@ -180,9 +206,10 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                                 kept |= (unsigned long long)window_adaptive4_row<NB>(
                                             t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
                                         << (NB * j3);
+                        kept &= okj;
                         if (kept)
                             ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
-                                           ((unsigned long long)j1 << 40) | kept;
+                                           ((unsigned long long)j1 << 40) | tri_bits | kept;
                         continue;
                     }
                     float t2[NB];
@@ -205,7 +232,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             le_lo |= (unsigned long long)(ad <= a.lo32) << (NB * j3 + j2);
                             le_hi |= (unsigned long long)(ad <= a.hi32) << (NB * j3 + j2);
                         }
-                    unsigned long long sure = le_lo & okm, amb = le_hi & ~le_lo & okm;
+                    unsigned long long sure = le_lo & okj, amb = le_hi & ~le_lo & okj;
                     while (amb) {                                // rare: exact FP64 decision
                         const int k = __ffsll(amb) - 1;
                         amb &= amb - 1;
@@ -216,7 +243,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     }
                     if (sure)
                         ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
-                                       ((unsigned long long)j1 << 40) | sure;
+                                       ((unsigned long long)j1 << 40) | tri_bits | sure;
                 }
             }
             int total;
@@ -228,6 +255,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 ++acc_ent;
                 const unsigned long long e = sQ[it];
                 const int iq2 = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
+                const int tri = (int)((e >> 36) & 3u);
                 const int4 cc2 = t.qc[iq2];
                 const int iq3 = q_index_near(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
                                              t.mesh[0], t.mesh[1], t.mesh[2]);
@@ -338,9 +366,12 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             w = sym4<float>(ch) * occupation_factor<float>(ch, n1f, occ[m2], n3) * gs *
                                 iw01 * (invw[m2] * iw3);
                         }
+                        // weight of the representative: 2 for a swapped pair, 1 on the diagonal
+                        const int wt = tri == 0 ? 1 : tri == 1 ? 2 : tri == 2 ? (j2 < j3 ? 2 : 1) : (j2 > j1 ? 2 : 1);
+                        w *= (R)wt;
                         acc_wp.add(w);
                         acc_g.add(w * (V.x * V.x + V.y * V.y));
-                        acc_n += 1;
+                        acc_n += wt;
                     }
                 }
             }

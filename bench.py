@@ -163,11 +163,12 @@ TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.114713e9 + 22.477824e6) / 279936,
 
 
 def flops_alg(stats, info, nb):
-    """Algorithmic FP32 flops of the four-phonon path per channel, counted for the factored
-    contraction it performs (complex multiply-add = 8 flops, real x complex = 4):
-      window          2 per candidate (add, subtract; the comparison is not counted)
-      W per (λ, q')   Φ~ = Σ_α Φ e_λ: nc4·27·3·4 / 8 (built once per 8 q'), plus
-                      W_r = Σ_c phase Σ_β e' Φ~: nc4·nb·9·(3 + 1)·8
+    """Algorithmic FP32 flops of the four-phonon path per channel, counted for the work it
+    performs (complex multiply-add = 8 flops, real x complex = 4); where the triangular domain
+    applies only the visited candidates and the evaluated processes count:
+      window          2 per visited candidate (add, subtract; the comparison is not counted)
+      W per (λ, q')   Φ~ = Σ_α Φ e_λ: nc4·27·3·4 / 8 (built once per 8 q'), plus the phase
+                      fold Ψ_rb = Σ_c phase Φ~: nc4·27·8, plus W = Σ_bβ e' Ψ: nb·n_keys·9·3na·8
       X per entry     n_keys·9·8 (X[c,d] = Σ_r P_r W_r)
       Y per item      nb²·8 (Y = X times the conjugated third-partner eigenvector)
       per process     V nb·8, weight 30"""
@@ -179,9 +180,10 @@ def flops_alg(stats, info, nb):
             continue
         cand = float(stats["candidates"][ch])
         units = cand / (N * nb ** 3)                   # (λ, q') units
-        w = units * (nc4 * 27 * 3 * 4 / 8.0 + nc4 * nb * 9 * 4 * 8)
-        out.append(2.0 * cand + w + stats["entries"][ch] * nk * 72.0 + stats["items"][ch] * nb * nb * 8.0
-                   + stats["kept"][ch] * (8.0 * nb + 30.0))
+        na = nb // 3
+        w = units * (nc4 * 27 * 3 * 4 / 8.0 + nc4 * 27 * 8 + nb * nk * 9 * na * 3 * 8)
+        out.append(2.0 * float(stats["visited"][ch]) + w + stats["entries"][ch] * nk * 72.0
+                   + stats["items"][ch] * nb * nb * 8.0 + stats["evaluated"][ch] * (8.0 * nb + 30.0))
     return out
 
 
@@ -336,6 +338,10 @@ def run_gpu(args):
               "vs_baseline": None, "dtype": "f32" if prec == MIXED else "f64",
               "data": "synthetic (seeded Morse diamond crystal)", "config": config_of(args, args.precision),
               "kept_4ph_per_step": kept4, "candidates_4ph_per_step": int(stats["candidates"][2:].sum()),
+              "evaluated_4ph_per_step": int(stats["evaluated"][2:].sum()),
+              "visited_4ph_candidates_per_step": int(stats["visited"][2:].sum()),
+              "domain": "triangular where the summand is partner-swap symmetric (one process of each "
+                        "swapped pair evaluated with weight 2); kept counts are the rectangular ones",
               "wall_s": wall, "gpu_launches": int(launches), "roofline": roof, "clocks": clocks}
 
     if not args.no_fp64 and world == 1:

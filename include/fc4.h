@@ -113,6 +113,13 @@ fc4_status fc4_get_modes(fc4_ctx *ctx, double *omega, double *vel, double *evec)
  *   V4 = Σ_c Σ Φ_c e_λ e^s1_λ' e^s2_λ'' e*_λ''' exp(i(s1 q'.R1 + s2 q''.R2 - q'''.R3)) / sqrt(m m m m)
  *   (e^+ = e, e^- = conj(e); C3 = ħπ/4, C4 = ħ²π/8 converted to ps^-1.)
  *
+ * Four-phonon sums use the triangular partner domain where the summand is swap-symmetric: the
+ * +- channel under (λ'', λ''') when Φ4 is invariant under exchanging cluster legs 2 and 3, the ++
+ * and -- channels under (λ', λ'') when Φ4 is invariant under exchanging legs 1 and 2 and σ is
+ * fixed (checked on the host to 1e-12 of max |Φ4| at fc4_init and fc4_update_anharmonic).  One
+ * process of each swapped pair is evaluated with weight 2; counts and Γ are those of the
+ * rectangular sum (Γ to rounding).
+ *
  * T_K > 0.  sigma_adaptive = 0: fixed Gaussian width sigma_value in THz (σ = 2π sigma_value
  * rad/ps).  sigma_adaptive = 1: adaptive width per process from the group velocities of the two
  * legs that the free partner sum moves together (3ph: λ', λ''; 4ph: λ'', λ'''),
@@ -194,10 +201,17 @@ fc4_status fc4_rates_backward(fc4_ctx *ctx, const double *dL_dgamma, double *dph
 fc4_status fc4_update_anharmonic(fc4_ctx *ctx, const double *phi3, const double *phi4);
 
 /* fc4_stats - work counters of the last fc4_rates call (synchronises the device), for channels
- * ch = 0..4: out[4*ch + 0] kept processes, out[4*ch + 1] four-phonon (q'', j''') items
- * evaluated, out[4*ch + 2] candidate tuples before the window, out[4*ch + 3] four-phonon
- * (q'', j') entries whose cluster sum was contracted (items and entries are 0 for 3ph). */
-fc4_status fc4_stats(fc4_ctx *ctx, long long out[20]);
+ * ch = 0..4:
+ *   out[6*ch + 0] kept processes of the rectangular partner domain (the counts of fc4_rates);
+ *   out[6*ch + 1] four-phonon (q'', j''') items evaluated;
+ *   out[6*ch + 2] candidate tuples of the rectangular domain before the window;
+ *   out[6*ch + 3] four-phonon (q'', j') entries whose cluster sum was contracted;
+ *   out[6*ch + 4] processes actually evaluated: where a partner-swap symmetry of the summand
+ *                 holds (see fc4_rates), one process of each swapped pair is evaluated and
+ *                 counted twice in out[6*ch + 0];
+ *   out[6*ch + 5] candidate tuples the energy-window test visited.
+ * Items and entries are 0 for 3ph. */
+fc4_status fc4_stats(fc4_ctx *ctx, long long out[30]);
 
 /* fc4_timings - device time in ms of the kernels launched by the last fc4_rates / fc4_kappa
  * calls, measured with CUDA events recorded on the launching stream around each launch (needs

@@ -206,13 +206,14 @@ class Engine:
         self._check(self.lib.fc4_set_block_threads(self.ctx, int(n)))
 
     def stats(self) -> dict:
-        """Work counters of the last rates call: kept processes, 4ph items and candidates per
-        channel (synchronises the device)."""
-        out = np.zeros(20, np.int64)
+        """Work counters of the last rates call per channel (synchronises the device): kept
+        processes and candidates of the rectangular domain, 4ph items and entries, processes
+        evaluated and candidates visited (fewer where the triangular domain applies)."""
+        out = np.zeros(30, np.int64)
         self._check(self.lib.fc4_stats(self.ctx, _ptr(out)))
-        o = out.reshape(5, 4)
+        o = out.reshape(5, 6)
         return {"kept": o[:, 0].copy(), "items": o[:, 1].copy(), "candidates": o[:, 2].copy(),
-                "entries": o[:, 3].copy()}
+                "entries": o[:, 3].copy(), "evaluated": o[:, 4].copy(), "visited": o[:, 5].copy()}
 
     def timings(self) -> dict:
         """Per-kernel device times (ms) of the last rates / kappa calls and the launch count."""

@@ -73,8 +73,9 @@ struct fc4_ctx {
     // scratch
     double *part_g = nullptr, *part_wp = nullptr;
     long long *part_n = nullptr, *part_items = nullptr, *part_ent = nullptr;
+    long long *part_ev = nullptr, *part_cev = nullptr;
     size_t part_cap = 0;
-    unsigned long long *stats = nullptr;    // [15] kept, items, entries per channel of the last call
+    unsigned long long *stats = nullptr;    // [25] kept, items, entries, evaluated, visited per channel
     long long cand[5] = {0, 0, 0, 0, 0};    // candidates per channel of the last call
     int *modes = nullptr;
     size_t modes_cap = 0;
@@ -680,16 +681,18 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     const size_t need = (size_t)5 * nm * N;
     if (need > c->part_cap) {
         for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items,
-                        (void *)c->part_ent})
+                        (void *)c->part_ent, (void *)c->part_ev, (void *)c->part_cev})
             if (p) { cudaFree(p); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), p)); }
         c->part_g = c->part_wp = nullptr;
-        c->part_n = c->part_items = c->part_ent = nullptr;
+        c->part_n = c->part_items = c->part_ent = c->part_ev = c->part_cev = nullptr;
         c->part_cap = 0;
         FC4_CUDA(c, dalloc(c, &c->part_g, need));
         FC4_CUDA(c, dalloc(c, &c->part_wp, need));
         FC4_CUDA(c, dalloc(c, &c->part_n, need));
         FC4_CUDA(c, dalloc(c, &c->part_items, need));
         FC4_CUDA(c, dalloc(c, &c->part_ent, need));
+        FC4_CUDA(c, dalloc(c, &c->part_ev, need));
+        FC4_CUDA(c, dalloc(c, &c->part_cev, need));
         c->part_cap = need;
     }
     if (modes != c->modes_on_device) {      // unchanged subsets need no copy (stream capture)
@@ -707,6 +710,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     a.part_n = c->part_n;
     a.part_items = c->part_items;
     a.part_ent = c->part_ent;
+    a.part_ev = c->part_ev;
+    a.part_cev = c->part_cev;
     size_t w_per_mode = 0;
     {   // W scratch of the tiled 4ph path, in whole modes, grown on demand: up to a quarter of the
         // device memory (at least 4 GiB), so that typical mode sets fit in one chunk and the ++ and
@@ -736,8 +741,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         a.wbuf = c->wbuf;
         a.wbuf_bytes = c->wbuf_bytes;
     }
-    if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 15));
-    FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 15 * sizeof(unsigned long long), s));
+    if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 25));
+    FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 25 * sizeof(unsigned long long), s));
     const int fp64 = c->precision == FC4_FP64;
     for (int ch = 0; ch < 5; ++ch) {
         if (!((channel_mask >> ch) & 1)) continue;
@@ -746,7 +751,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
                 FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
                 FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
                 FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_items + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                for (long long *p : {c->part_items, c->part_ent, c->part_ev, c->part_cev})
+                    FC4_CUDA(c, cudaMemsetAsync(p + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
                 continue;
             }
             Timed tm(c, ch, s);
@@ -756,7 +762,8 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
                 FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
                 FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
                 FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_items + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+                for (long long *p : {c->part_items, c->part_ent, c->part_ev, c->part_cev})
+                    FC4_CUDA(c, cudaMemsetAsync(p + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
                 continue;
             }
             const int s1 = ch == 4 ? -1 : 1;
@@ -938,17 +945,19 @@ fc4_status fc4_update_anharmonic(fc4_ctx *c, const double *phi3, const double *p
     return FC4_OK;
 }
 
-fc4_status fc4_stats(fc4_ctx *c, long long out[20]) {
+fc4_status fc4_stats(fc4_ctx *c, long long out[30]) {
     if (!c || !out) return fail(c, FC4_ERR_INVALID, "NULL argument");
     if (!c->have_last || !c->stats) return fail(c, FC4_ERR_STATE, "fc4_stats before fc4_rates");
-    unsigned long long h[15];
+    unsigned long long h[25];
     FC4_CUDA(c, cudaDeviceSynchronize());
     FC4_CUDA(c, cudaMemcpy(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int ch = 0; ch < 5; ++ch) {
-        out[4 * ch] = (long long)h[3 * ch];
-        out[4 * ch + 1] = (long long)h[3 * ch + 1];
-        out[4 * ch + 2] = c->cand[ch];
-        out[4 * ch + 3] = (long long)h[3 * ch + 2];
+        out[6 * ch] = (long long)h[5 * ch];
+        out[6 * ch + 1] = (long long)h[5 * ch + 1];
+        out[6 * ch + 2] = c->cand[ch];
+        out[6 * ch + 3] = (long long)h[5 * ch + 2];
+        out[6 * ch + 4] = (long long)h[5 * ch + 3];
+        out[6 * ch + 5] = (long long)h[5 * ch + 4];
     }
     return FC4_OK;
 }

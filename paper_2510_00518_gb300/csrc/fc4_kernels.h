@@ -71,6 +71,8 @@ struct RateArgs {
     long long *part_n;           // kept processes
     long long *part_items;       // 4ph: (q'', j''') items evaluated; 3ph: 0
     long long *part_ent;         // 4ph: (q'', j') entries whose X or Y was contracted; 3ph: 0
+    long long *part_ev;          // processes evaluated (kept counts a swap pair twice); may be NULL
+    long long *part_cev;         // candidates visited by the window; may be NULL
     int n_part[5];               // partial slots written per mode for each channel (<= N)
     void *wbuf;                  // optional scratch for the tiled 4ph path (W per (λ, q')); may be NULL
     size_t wbuf_bytes;

@@ -265,14 +265,15 @@ struct int5 { int a, b, c, d, e; };
 // butterfly; Γ = C / N^k * Σ, WP = Σ / N^k (k = 1 for 3ph, 2 for 4ph).
 __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask, double c3, double c4,
                               const double *part_g, const double *part_wp, const long long *part_n,
-                              const long long *part_items, const long long *part_ent, double *gamma,
-                              double *wp, long long *counts, unsigned long long *stats, const int *err) {
+                              const long long *part_items, const long long *part_ent, const long long *part_ev,
+                              const long long *part_cev, double *gamma, double *wp, long long *counts,
+                              unsigned long long *stats, const int *err) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= 5 * n_modes) return;
     const int ch = w / n_modes, ms = w - ch * n_modes;
     double g = 0.0, p = 0.0;
-    long long n = 0, it = 0, en = 0;
+    long long n = 0, it = 0, en = 0, ev = 0, cv = 0;
     if ((channel_mask >> ch) & 1) {
         const size_t base = ((size_t)ch * n_modes + ms) * N;
         const int np = ch == 0 ? n_part.a : ch == 1 ? n_part.b : ch == 2 ? n_part.c : ch == 3 ? n_part.d : n_part.e;
@@ -282,6 +283,8 @@ __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask,
             n += part_n[base + q];
             it += part_items[base + q];
             en += part_ent[base + q];
+            if (part_ev) ev += part_ev[base + q];
+            if (part_cev) cv += part_cev[base + q];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -290,12 +293,16 @@ __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask,
             n += __shfl_xor_sync(kFull, n, o);
             it += __shfl_xor_sync(kFull, it, o);
             en += __shfl_xor_sync(kFull, en, o);
+            ev += __shfl_xor_sync(kFull, ev, o);
+            cv += __shfl_xor_sync(kFull, cv, o);
         }
     }
     if (lane == 0 && stats) {
-        atomicAdd(stats + 3 * ch, (unsigned long long)n);       // integer sums: order-independent
-        atomicAdd(stats + 3 * ch + 1, (unsigned long long)it);
-        atomicAdd(stats + 3 * ch + 2, (unsigned long long)en);
+        atomicAdd(stats + 5 * ch, (unsigned long long)n);       // integer sums: order-independent
+        atomicAdd(stats + 5 * ch + 1, (unsigned long long)it);
+        atomicAdd(stats + 5 * ch + 2, (unsigned long long)en);
+        atomicAdd(stats + 5 * ch + 3, (unsigned long long)ev);
+        atomicAdd(stats + 5 * ch + 4, (unsigned long long)cv);
     }
     if (lane == 0) {
         const double norm = ch < 2 ? (double)N : (double)N * (double)N;
@@ -317,7 +324,7 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
     np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
     reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
-        gamma, wp, counts, stats, a.err);
+        a.part_ev, a.part_cev, gamma, wp, counts, stats, a.err);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,8 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
         a.part_n[o] = n;
         a.part_items[o] = 0;
         a.part_ent[o] = 0;
+        if (a.part_ev) a.part_ev[o] = n;
+        if (a.part_cev) a.part_cev[o] = (long long)N * NB * NB;
     }
 }
 

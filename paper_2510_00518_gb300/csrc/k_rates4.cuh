@@ -395,6 +395,8 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
         a.part_n[o] = n;
         a.part_items[o] = ni;
         a.part_ent[o] = ne;
+        if (a.part_ev) a.part_ev[o] = n;                           // the rectangular domain
+        if (a.part_cev) a.part_cev[o] = (long long)N * NB * NB * NB;
     }
 }
 

@@ -434,6 +434,8 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
             a.part_n[o] = cnts[0];
             a.part_items[o] = cnts[1];
             a.part_ent[o] = cnts[2];
+            if (a.part_ev) a.part_ev[o] = cnts[0];                 // the rectangular domain
+            if (a.part_cev) a.part_cev[o] = (long long)N * NB * NB * NB;
         }
     }
     if (dead && tid == 0) {
@@ -447,6 +449,8 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
             a.part_n[o] = 0;
             a.part_items[o] = 0;
             a.part_ent[o] = 0;
+            if (a.part_ev) a.part_ev[o] = 0;
+            if (a.part_cev) a.part_cev[o] = 0;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

@@ -120,7 +120,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB * kQPT]
     __shared__ int s_scan[32];
     __shared__ double s_red[2 * 32];
-    __shared__ long long s_redn[3 * 32];
+    __shared__ long long s_redn[5 * 32];
 
     const int unit = blockIdx.x;                                // (mode - mode0) * N + q'
     const int ml = unit / N, q1 = unit - ml * N;
@@ -133,7 +133,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     const R *invw = Sel<R>::invw(t);
 
     Acc<R> acc_g, acc_wp;
-    long long acc_n = 0, acc_items = 0, acc_ent = 0;
+    long long acc_n = 0, acc_items = 0, acc_ent = 0, acc_ev = 0, acc_cev = 0;
     const unsigned vm1 = t.vmask[q1];
 
     if (!(q0 == 0 && j0 < 3) && vm1) {
@@ -177,6 +177,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     if (q2 < q1) continue;                       // the swap of (q2, q1)
                     tri = q2 > q1 ? 1 : 3;
                 }
+                acc_cev += NB * NB * NB;                         // this q'' is visited
                 // (j'', j''') pairs whose two partners both take part: bit NB j''' + j''
                 unsigned long long okm = 0;
 #pragma unroll
@@ -372,6 +373,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         acc_wp.add(w);
                         acc_g.add(w * (V.x * V.x + V.y * V.y));
                         acc_n += wt;
+                        acc_ev += 1;
                     }
                 }
             }
@@ -379,8 +381,8 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
         }
     }
     double sums[2] = {acc_g.value(), acc_wp.value()};
-    long long cnts[3] = {acc_n, acc_items, acc_ent};
-    block_sum_multi<2, 3>(sums, cnts, s_red, s_redn);
+    long long cnts[5] = {acc_n, acc_items, acc_ent, acc_ev, acc_cev};
+    block_sum_multi<2, 5>(sums, cnts, s_red, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
         a.part_g[o] = sums[0];
@@ -388,6 +390,8 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
         a.part_n[o] = cnts[0];
         a.part_items[o] = cnts[1];
         a.part_ent[o] = cnts[2];
+        if (a.part_ev) a.part_ev[o] = cnts[3];
+        if (a.part_cev) a.part_cev[o] = cnts[4];
     }
 }
 

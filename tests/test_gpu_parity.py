@@ -208,3 +208,26 @@ def test_sharded_rates_kappa_single_process(eng3, oracle3_all, prob3):
     assert np.array_equal(qs, np.arange(27))
     kr = prob3.kappa(oracle3_all[0].sum(0))
     assert np.abs(k.cpu().numpy() - kr).max() <= 1e-10 * np.abs(kr).max()
+
+
+def test_triangular_domain_matches_rectangle(sys0, prob3):
+    """Partner-swap symmetric Φ4: one process per swapped pair is evaluated (stats), with the
+    rectangular kept counts and Γ.  Breaking the leg-exchange symmetry of one cluster entry by
+    1e-9 turns the triangle off (every kept process evaluated) and moves Γ by that much only."""
+    G = prob3.rates()[0]
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        e = make_engine(sys0, (3, 3, 3), precision=prec, prob=prob3)
+        g_tri, _, c_tri = e.rates(300.0, 0.1, 0b11100)
+        st = e.stats()
+        assert np.array_equal(c_tri.cpu().numpy()[2:], prob3.rates(channel_mask=0b11100)[2][2:])
+        assert all(st["evaluated"][ch] < st["kept"][ch] for ch in (2, 3, 4))
+        assert_close(g_tri.cpu().numpy()[2:], G[2:], tol, floor_frac=1e-6 if prec else 1e-12, what="triangle")
+        p4 = sys0[3].phi.copy()
+        p4[7, 13] *= 1.0 + 1e-9
+        e.update_anharmonic(None, p4)
+        g_rect, _, c_rect = e.rates(300.0, 0.1, 0b11100)
+        st = e.stats()
+        assert all(st["evaluated"][ch] == st["kept"][ch] for ch in (2, 3, 4))
+        assert np.array_equal(c_rect.cpu().numpy(), c_tri.cpu().numpy())
+        assert_close(g_rect.cpu().numpy()[2:], g_tri.cpu().numpy()[2:], 1e-5 if prec else 1e-8,
+                     floor_frac=1e-6 if prec else 1e-12, what="rectangle vs triangle")

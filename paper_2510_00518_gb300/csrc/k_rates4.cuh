@@ -80,17 +80,46 @@ __device__ __forceinline__ float delta_comp(float h0, float l0, float h1, float 
     return x3 + ((e1 + e2) + (e3 + lo));
 }
 
-// Window masks of one q'': bit j'' of mask[j'''] is set iff the process is kept.  FP32 prefilter
-// with the proven bound; candidates inside the band are decided by the exact FP64 Δ.
+// Triangular domain of a (q', q'') pair (partner-swap symmetry of the summand): -1 the pair is the
+// swap of one evaluated elsewhere; 0 no symmetry used (weight 1); 1 weight 2; 2 +- with q'' = q'''
+// (keep j'' <= j'''); 3 ++ / -- with q'' = q' (keep j'' >= j').
+__device__ __forceinline__ int tri_code(const RateArgs &a, int ch, int q1, int q2, int q3) {
+    if (ch == 3) {
+        if (!(a.tri & 1)) return 0;
+        return q2 > q3 ? -1 : (q2 < q3 ? 1 : 2);
+    }
+    if (!(a.tri & 2)) return 0;
+    return q2 < q1 ? -1 : (q2 > q1 ? 1 : 3);
+}
+
+// weight of an evaluated process: 2 for a swapped pair, 1 on the diagonal or without symmetry
+__device__ __forceinline__ int tri_weight(int tri, int j1, int j2, int j3) {
+    return tri == 0 ? 1 : tri == 1 ? 2 : tri == 2 ? (j2 < j3 ? 2 : 1) : (j2 > j1 ? 2 : 1);
+}
+
+// Window masks of one q'': bit j'' of mask[j'''] is set iff the process is kept (restricted to the
+// triangular domain).  FP32 prefilter with the proven bound; candidates inside the band are
+// decided by the exact FP64 Δ.
 template <int NB, bool ADA>
 __device__ __forceinline__ int window_masks(const Tables &t, const RateArgs &a, int ch, int s2,
                                             float base32, int m0, int m1, double w0, double w1, int q2,
                                             int q3, unsigned (&mask)[NB]) {
     const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
+    const int q1 = m1 / NB, j1 = m1 - q1 * NB;
+    const int tri = tri_code(a, ch, q1, q2, q3);
+    if (tri < 0) {
+#pragma unroll
+        for (int j3 = 0; j3 < NB; ++j3) mask[j3] = 0u;
+        return 0;
+    }
+    // branch pairs of the domain: j'' <= j''' (tri 2) or j'' >= j' (tri 3)
+    auto dom = [&](int j3) -> unsigned {
+        return tri == 2 ? (2u << j3) - 1u : tri == 3 ? ~((1u << j1) - 1u) : ~0u;
+    };
     if constexpr (ADA) {
         int n = 0;
         for (int j3 = 0; j3 < NB; ++j3) {
-            mask[j3] = ((v3 >> j3) & 1u) ? window_adaptive4_row<NB>(t, a, ch, s2, base32, m0, m1, q2, q3 * NB + j3, v2)
+            mask[j3] = ((v3 >> j3) & 1u) ? window_adaptive4_row<NB>(t, a, ch, s2, base32, m0, m1, q2, q3 * NB + j3, v2) & dom(j3)
                                          : 0u;
             n += (mask[j3] != 0);
         }
@@ -118,8 +147,8 @@ __device__ __forceinline__ int window_masks(const Tables &t, const RateArgs &a, 
                 m |= (unsigned)keep << j2;
             }
         }
-        mask[j3] = m;
-        n += (m != 0);
+        mask[j3] = m & dom(j3);
+        n += (mask[j3] != 0);
     }
     return n;
 }
@@ -176,7 +205,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const R *invw = Sel<R>::invw(t);
 
     Acc<R> acc_g, acc_wp;
-    long long acc_n = 0, acc_items = 0, acc_ent = 0;
+    long long acc_n = 0, acc_items = 0, acc_ent = 0, acc_ev = 0, acc_cev = 0;
 
     const bool active = !(q0 == 0 && j0 < 3);
     if (active) {
@@ -237,6 +266,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                     unsigned mask[NB];
+                    if (tri_code(a, ch, q1, q2, q3) >= 0) acc_cev += NB * NB;   // visited
                     if (window_masks<NB, ADA>(t, a, ch, s2, base32, m0, m1, w0, w1, q2, q3, mask) > 0) {
                         if constexpr (XROUTE) {
                             unsigned long long e = (unsigned long long)q2 << 40;
@@ -271,6 +301,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                     unsigned mask[NB];
+                    const int tri = tri_code(a, ch, q1, iq2, q3);
                     if constexpr (XROUTE) {
 #pragma unroll
                         for (int j3 = 0; j3 < NB; ++j3) mask[j3] = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);
@@ -373,9 +404,12 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                                 w = sym4<float>(ch) * occupation_factor<float>(ch, occ[m1], occ[m2], n3) * g *
                                     (invw[m0] * invw[m1]) * (invw[m2] * iw3);
                             }
+                            const int wt = tri_weight(tri, j1, j2, j3);
+                            w *= (R)wt;
                             acc_wp.add(w);
                             acc_g.add(w * (V.x * V.x + V.y * V.y));
-                            acc_n += 1;
+                            acc_n += wt;
+                            acc_ev += 1;
                         }
                     }
                 }
@@ -388,6 +422,8 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const long long n = block_sum(acc_n, s_redn);
     const long long ni = block_sum(acc_items, s_redn);
     const long long ne = block_sum(acc_ent, s_redn);
+    const long long nev = block_sum(acc_ev, s_redn);
+    const long long ncv = block_sum(acc_cev, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
         a.part_g[o] = g;
@@ -395,8 +431,8 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
         a.part_n[o] = n;
         a.part_items[o] = ni;
         a.part_ent[o] = ne;
-        if (a.part_ev) a.part_ev[o] = n;                           // the rectangular domain
-        if (a.part_cev) a.part_cev[o] = (long long)N * NB * NB * NB;
+        if (a.part_ev) a.part_ev[o] = nev;
+        if (a.part_cev) a.part_cev[o] = ncv;
     }
 }
 

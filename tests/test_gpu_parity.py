@@ -222,8 +222,14 @@ def test_triangular_domain_matches_rectangle(sys0, prob3):
         assert np.array_equal(c_tri.cpu().numpy()[2:], prob3.rates(channel_mask=0b11100)[2][2:])
         assert all(st["evaluated"][ch] < st["kept"][ch] for ch in (2, 3, 4))
         assert_close(g_tri.cpu().numpy()[2:], G[2:], tol, floor_frac=1e-6 if prec else 1e-12, what="triangle")
+        # an entry with distinct Cartesian indices on legs 1, 2 and on legs 2, 3, so that both
+        # leg exchanges map it to another entry (the on-site Φ[αααα] terms map to themselves)
         p4 = sys0[3].phi.copy()
-        p4[7, 13] *= 1.0 + 1e-9
+        k = np.arange(81)
+        be, ga, de = (k // 9) % 3, (k // 3) % 3, k % 3
+        cand = np.where((be != ga) & (ga != de), np.abs(p4), 0.0)
+        i, k = np.unravel_index(cand.argmax(), cand.shape)
+        p4[i, k] *= 1.0 + 1e-9                        # well above the 1e-12 symmetry tolerance
         e.update_anharmonic(None, p4)
         g_rect, _, c_rect = e.rates(300.0, 0.1, 0b11100)
         st = e.stats()

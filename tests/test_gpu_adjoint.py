@@ -90,3 +90,40 @@ def test_kappa_gradient_autograd_vs_finite_differences(sysm):
         noise = 1e-15 * abs(float(k.detach())) / h            # rounding of κ, amplified by the difference
         assert abs(fd - an) <= 1e-6 * abs(an) + noise, (order, c, x, fd, an, noise)
     e.update_anharmonic(sysm[2].phi, sysm[3].phi)
+
+
+def test_rates_gradient_8cubed_finite_differences(sysm):
+    """The differentiation workload on the 8x8x8 mesh: dL/dΦ of L = Σ_ch,λ G Γ_ch(λ) over the six
+    modes of one seeded q point (FP64), against central differences of the GPU forward pass on 16
+    seeded cluster entries (8 of Φ3, 8 of Φ4; h = 1e-5 relative)."""
+    from synth.sampling import sample_q
+    mesh = (8, 8, 8)
+    e = make_engine(sysm, mesh, precision=0, inject=False)
+    sub = sample_q(512, 1, seed=5).tolist()
+    G = torch.tensor(np.random.default_rng(8).standard_normal((5, 6)), device="cuda")
+    g0, _, _ = e.rates(300.0, 0.1, 31, q_subset=sub)
+    d3, d4 = e.backward(G)
+    d3, d4 = d3.cpu().numpy(), d4.cpu().numpy()
+    p3, p4 = sysm[2].phi.copy(), sysm[3].phi.copy()
+    L0 = float((G * g0).sum())
+    rng = np.random.default_rng(21)
+    picks = [(3, int(c), int(x)) for c, x in zip(rng.integers(0, p3.shape[0], 8), rng.integers(0, 27, 8))] + \
+            [(4, int(c), int(x)) for c, x in zip(rng.integers(0, p4.shape[0], 8), rng.integers(0, 81, 8))]
+    try:
+        for order, c, x in picks:
+            base = p3 if order == 3 else p4
+            h = 1e-5 * max(abs(float(base[c, x])), 1.0)
+            vals = []
+            for sgn in (1, -1):
+                mod = base.copy()
+                mod[c, x] += sgn * h
+                e.update_anharmonic(mod if order == 3 else None, mod if order == 4 else None)
+                g, _, _ = e.rates(300.0, 0.1, 31, q_subset=sub)
+                vals.append(float((G * g).sum()))
+            e.update_anharmonic(p3 if order == 3 else None, p4 if order == 4 else None)
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = float((d3 if order == 3 else d4)[c, x])
+            noise = 1e-14 * abs(L0) / h
+            assert abs(fd - an) <= 1e-6 * abs(an) + noise, (order, c, x, fd, an, noise)
+    finally:
+        e.update_anharmonic(p3, p4)

@@ -12,7 +12,8 @@
 // contraction.  B is built once per unit, A once per round; one thread issues tcgen05.mma
 // (kind::f16) and tcgen05.commit to an mbarrier.  The three warpgroups then share the 128 rows:
 // warpgroup g reads X of partner branches j' = g and g + 3 for its row with tcgen05.ld and
-// evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights).
+// evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights),
+// on the triangular domain of the channel when Φ4 allows it (one row of each swapped pair).
 //
 // Waits on the mbarrier are bounded (fc4_options.timeout_cycles SM clocks, default 2e9); on expiry
 // the kernel sets the context's error flag (the reduction then writes NaN into Γ), waits once
@@ -141,7 +142,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
     __shared__ __align__(8) unsigned long long s_mbar;
     __shared__ uint32_t s_tmem;
     __shared__ double s_red[2 * 32];
-    __shared__ long long s_redn[3 * 32];
+    __shared__ long long s_redn[5 * 32];
     __shared__ float s_wmax[kTcThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -179,7 +180,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
         const int m0 = a.modes[ms];
         const int q0 = m0 / NB, j0 = m0 - q0 * NB;
         Acc<float> acc_g, acc_wp;
-        long long acc_n = 0, acc_items = 0, acc_ent = 0;
+        long long acc_n = 0, acc_items = 0, acc_ent = 0, acc_ev = 0, acc_cev = 0;
         const unsigned vm1 = t.vmask[q1];
         if (!(q0 == 0 && j0 < 3) && vm1) {                       // uniform across the block
             const float2 *wsrc = wall + (size_t)unit * (NB * nk * 9);
@@ -255,7 +256,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                 }
                 // window of this row for the warpgroup's partner branches: bit NB j3 + j2 set iff kept
                 unsigned long long keep[2] = {0ull, 0ull};
-                int q3 = 0;
+                int q3 = 0, tri = -1;
                 if (valid) {
                     const int4 c2 = t.qc[q2];
                     q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z, t.mesh[0], t.mesh[1], t.mesh[2]);
@@ -266,10 +267,18 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                         w2f[j] = (float)s2 * t.om32[q2 * NB + j];
                         w3f[j] = t.om32[q3 * NB + j];
                     }
+                    // triangular domain of +- (λ'' <-> λ'''), as in the CUDA-core kernels
+                    tri = tri_code(a, ch, q1, q2, q3);
                     unsigned long long okm = 0;
 #pragma unroll
                     for (int j3 = 0; j3 < NB; ++j3)
-                        if ((v3 >> j3) & 1u) okm |= (unsigned long long)(v2 & ((1u << NB) - 1u)) << (NB * j3);
+                        if ((v3 >> j3) & 1u) {
+                            unsigned row = v2 & ((1u << NB) - 1u);
+                            if (tri == 2) row &= (2u << j3) - 1u;        // j'' <= j'''
+                            okm |= (unsigned long long)row << (NB * j3);
+                        }
+                    if (tri < 0) okm = 0;                                // the swap of another row
+                    else acc_cev += (long long)nj * NB * NB;
 #pragma unroll
                     for (int jj = 0; jj < nj; ++jj) {
                         const int j1 = wg + 3 * jj;
@@ -282,7 +291,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                                     kept |= (unsigned long long)window_adaptive4_row<NB>(
                                                 t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
                                             << (NB * j3);
-                            keep[jj] = kept;
+                            keep[jj] = kept & okm;
                         } else {
                             float t2[NB];
 #pragma unroll
@@ -414,9 +423,11 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                             else gs = __expf(-(df * df) * a.inv_sigma2_32) * a.gnorm32;
                             const float w = sym4<float>(ch) * occupation_factor<float>(ch, n1f, occ[m2], n3) * gs *
                                             iw01 * (invw[m2] * iw3);
-                            acc_wp.add(w);
-                            acc_g.add(w * (V.x * V.x + V.y * V.y));
-                            acc_n += 1;
+                            const int wt = tri_weight(tri, j1, j2, j3);
+                            acc_wp.add(w * (float)wt);
+                            acc_g.add((w * (float)wt) * (V.x * V.x + V.y * V.y));
+                            acc_n += wt;
+                            acc_ev += 1;
                         }
                     }
                 }
@@ -425,8 +436,8 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
             }
         }
         double sums[2] = {acc_g.value(), acc_wp.value()};
-        long long cnts[3] = {acc_n, acc_items, acc_ent};
-        block_sum_multi<2, 3>(sums, cnts, s_red, s_redn);
+        long long cnts[5] = {acc_n, acc_items, acc_ent, acc_ev, acc_cev};
+        block_sum_multi<2, 5>(sums, cnts, s_red, s_redn);
         if (tid == 0) {
             const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
             a.part_g[o] = sums[0];
@@ -434,8 +445,8 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
             a.part_n[o] = cnts[0];
             a.part_items[o] = cnts[1];
             a.part_ent[o] = cnts[2];
-            if (a.part_ev) a.part_ev[o] = cnts[0];                 // the rectangular domain
-            if (a.part_cev) a.part_cev[o] = (long long)N * NB * NB * NB;
+            if (a.part_ev) a.part_ev[o] = cnts[3];
+            if (a.part_cev) a.part_cev[o] = cnts[4];
         }
     }
     if (dead && tid == 0) {

@@ -32,9 +32,15 @@ def test_tc_matches_cuda_cores_and_oracle(sys0, mesh):
     sub = sample_q(n, 3, seed=n).tolist()
     e.set_tensor_cores(True)
     g1, w1, c1 = (x.cpu().numpy() for x in e.rates(300.0, 0.1, PM, q_subset=sub))
+    st1 = e.stats()
     e.set_tensor_cores(False)
     g0, w0, c0 = (x.cpu().numpy() for x in e.rates(300.0, 0.1, PM, q_subset=sub))
+    st0 = e.stats()
     assert c1[3].sum() > 0
+    # both contractions walk the same triangular domain (q'' <= q''') of the +- channel
+    for k in ("kept", "evaluated"):
+        assert st1[k][3] == st0[k][3], k
+    assert st1["evaluated"][3] < st1["kept"][3]
     assert np.array_equal(c1, c0)
     assert_close(g1, g0, 1e-5, floor_frac=1e-6, what="tensor vs CUDA cores")
     assert_close(w1, w0, 1e-5, floor_frac=1e-6, what="wp")

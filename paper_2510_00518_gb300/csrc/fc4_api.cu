@@ -523,10 +523,24 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
             const int d[3] = {std::get<1>(keys[k]), std::get<2>(keys[k]), std::get<3>(keys[k])};
             kr[k] = phase_vec(d, mesh, L);
         }
+        // the clusters of each (key, leg-1 atom), in cluster order: the W kernels' phase fold
+        std::vector<int> kb_start((size_t)nk * na + 1, 0), kb_idx(c->nc4);
+        for (int s = 0; s < c->nc4; ++s) {
+            const int r = key_id[ck[c->perm4[s]]];
+            kb_start[(size_t)r * na + at[s].y + 1]++;
+        }
+        for (size_t g = 0; g < (size_t)nk * na; ++g) kb_start[g + 1] += kb_start[g];
+        {
+            std::vector<int> fill(kb_start.begin(), kb_start.end() - 1);
+            for (int s = 0; s < c->nc4; ++s) {
+                const int r = key_id[ck[c->perm4[s]]];
+                kb_idx[fill[(size_t)r * na + at[s].y]++] = s;
+            }
+        }
         int4 *d_at, *d_r3, *d_r13, *d_kr;
         double *d_im;
         float *d_im32;
-        int *d_ks;
+        int *d_ks, *d_kbs, *d_kbi;
         FC4_TRY(upload(c, &d_at, at));
         FC4_TRY(upload(c, &d_r3, r3));
         FC4_TRY(upload(c, &d_r13, r13));
@@ -535,6 +549,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
         FC4_TRY(upload(c, &c->phi4, ph));
         FC4_TRY(upload(c, &c->phi4_32, ph32));
         FC4_TRY(upload(c, &d_ks, key_start));
+        FC4_TRY(upload(c, &d_kbs, kb_start));
+        FC4_TRY(upload(c, &d_kbi, kb_idx));
         FC4_TRY(upload(c, &d_kr, kr));
         FC4_TRY(upload(c, &c->perm4_dev, c->perm4));
         FC4_TRY(dalloc(c, &c->adj_tmp, 81 * (size_t)std::max(1, c->nc4)));
@@ -546,6 +562,8 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
         t.phi4 = c->phi4;
         t.phi4_32 = c->phi4_32;
         t.key_start = d_ks;
+        t.kb_start = d_kbs;
+        t.kb_idx = d_kbi;
         double2 *d_P4;
         float2 *d_P4_32;
         FC4_TRY(dalloc(c, &d_P4, (size_t)N * nk));

@@ -52,6 +52,8 @@ struct Tables {
     const double *phi4;          // [nc4][81]
     const float *phi4_32;
     const int *key_start;        // [n_keys + 1] cluster range of each key
+    const int *kb_start;         // [n_keys * n_atoms + 1] range in kb_idx of (key r, leg-1 atom b)
+    const int *kb_idx;           // [nc4] clusters grouped by (r, b), ascending within a group
     const double2 *P4;           // [N][n_keys] exp(i q.(R2 - R3)) of each key
     const float2 *P4_32;
     int grp_start[kGroups];      // key range of group g = c * n_atoms + d

@@ -254,7 +254,8 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
 
             const float base32 = w0f + (float)s1 * t.om32[m1];
             const double w1 = t.om[m1];
-            for (int qb = 0; qb < N; qb += kQChunk) {
+            // ++ and -- on their triangle (q'' >= q') start at q'' = q'
+            for (int qb = (ch != 3 && (a.tri & 2)) ? q1 : 0; qb < N; qb += kQChunk) {
                 const int qe = min(N, qb + kQChunk);
                 // pass 1: window masks of this thread's q''; the X-route keeps those with a kept
                 // process in a small local list (q'' packed with the 36 mask bits) and counts them

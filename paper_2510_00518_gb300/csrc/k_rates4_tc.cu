@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kTcRows = 128;                // q'' per round = MMA M = TMEM lanes
 constexpr int kTcThreads = 384;             // three warpgroups over the same 128 rows
+constexpr int kTcTriChunk = 4 * kTcThreads; // q'' per chunk of the triangle list
 constexpr int kTcN = 112;                   // MMA N per (c, d) group: 6 j' x 18 columns used
 constexpr int kTcCols = 512;                // TMEM columns: 4 groups x 112, allocated as 512
 
@@ -144,6 +145,8 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
     __shared__ double s_red[2 * 32];
     __shared__ long long s_redn[5 * 32];
     __shared__ float s_wmax[kTcThreads / 32];
+    __shared__ int s_scan[32];
+    __shared__ unsigned short s_tri[kTcTriChunk];               // triangle: q'' - chunk start
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid & (kTcRows - 1), wg = tid >> 7;         // TMEM lane = row; warpgroup
@@ -228,9 +231,36 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
             const double w0 = t.om[m0];
             const float w0f = t.om32[m0];
 
-            for (int qb = 0; qb < N && !dead; qb += kTcRows) {
-                const int q2 = qb + row;
-                const bool valid = q2 < N;
+            // On the triangle the rounds take only the q'' <= q''' (a list per chunk of q'', in
+            // ascending order), so the MMA, the A staging and the TMEM reads of the skipped half go too.
+            const bool pm_list = (a.tri & 1) != 0;
+            for (int cb = 0; cb < N && !dead; cb += pm_list ? kTcTriChunk : N) {
+              int cnt = N - cb;
+              if (pm_list) {
+                constexpr int kPer = kTcTriChunk / kTcThreads;
+                const int ce = min(N, cb + kTcTriChunk), lo = cb + tid * kPer;
+                unsigned fl = 0;
+                int nf = 0;
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const int qq = lo + i;
+                    if (qq < ce) {
+                        const int4 c2 = t.qc[qq];
+                        const int qr = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                                    t.mesh[0], t.mesh[1], t.mesh[2]);
+                        if (qq <= qr) { fl |= 1u << i; ++nf; }
+                    }
+                }
+                int off = block_exclusive_scan(nf, s_scan, &cnt);
+#pragma unroll
+                for (int i = 0; i < kPer; ++i)
+                    if ((fl >> i) & 1u) s_tri[off++] = (unsigned short)(tid * kPer + i);
+                __syncthreads();
+              }
+              for (int qb = 0; qb < cnt && !dead; qb += kTcRows) {
+                const int ix = qb + row;
+                const bool valid = ix < cnt;
+                const int q2 = valid ? cb + (pm_list ? (int)s_tri[ix] : ix) : 0;
                 // A: row `row`, the warpgroup's groups (0 | 1, 2 | 3: its share of the row), FP16 hi / lo
                 const float2 *Prow = t.P4_32 + (size_t)(valid ? q2 : 0) * nk;
                 for (int g = (wg == 0 ? 0 : wg == 1 ? 1 : 3); g <= (wg == 0 ? 0 : wg == 1 ? 2 : 3); ++g) {
@@ -433,6 +463,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncthreads();                                 // A and TMEM are reused next round
+              }
             }
         }
         double sums[2] = {acc_g.value(), acc_wp.value()};

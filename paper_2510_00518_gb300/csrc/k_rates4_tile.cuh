@@ -18,8 +18,8 @@ constexpr int kTileQ = 128;
 // partner points q'' per thread and compaction round: 4 for the sparse ++ and -- channels (more
 // window work per round), 2 for +- (fewer registers held across its dense entry work)
 constexpr int kQPTSparse = 4, kQPTDense = 2;
-
-__host__ __device__ inline int tile_key_stride(int n_keys) { return n_keys | 1; }
+// q'' per chunk of the +- triangle list (the q'' <= q''' of a unit, built in shared memory)
+constexpr int kTriChunk = 1024;
 
 
 // W[j'][r][γδ] of units (λ, q') for every partner branch j', written to global memory (layout
@@ -80,11 +80,12 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nk * NA * 27; k += blockDim.x) {
-            const int r = k / (NA * 27), rem = k - r * (NA * 27);
-            const int b = rem / 27, bgd = rem - b * 27;
+            const int rb = k / 27, bgd = k - rb * 27;            // rb = r NA + b
             C acc = czero<C>();
-            for (int c = t.key_start[r]; c < t.key_start[r + 1]; ++c)
-                if (t.c4_at[c].y == b) acc = cfma(sPh[c], sPt[c * 27 + bgd], acc);
+            for (int i = t.kb_start[rb]; i < t.kb_start[rb + 1]; ++i) {
+                const int c = t.kb_idx[i];
+                acc = cfma(sPh[c], sPt[c * 27 + bgd], acc);
+            }
             sPsi[k] = acc;
         }
         __syncthreads();
@@ -121,6 +122,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     __shared__ int s_scan[32];
     __shared__ double s_red[2 * 32];
     __shared__ long long s_redn[5 * 32];
+    __shared__ unsigned short s_tri[kTriChunk];                 // +- triangle: q'' - chunk start
 
     const int unit = blockIdx.x;                                // (mode - mode0) * N + q'
     const int ml = unit / N, q1 = unit - ml * N;
@@ -149,11 +151,39 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
 #pragma unroll
         for (int j = 0; j < NB; ++j) base32[j] = w0f + (float)s1 * t.om32[q1 * NB + j];
 
-        for (int qb = 0; qb < N; qb += kTileQ * kQPT) {
+        // The triangular domain is walked without idle lanes: ++ and -- start at q'' = q'; +- takes
+        // its q'' <= q''' from a list built per chunk of kTriChunk q'' (ascending order).
+        const bool pm_list = (ch == 3) && (a.tri & 1);
+        const int qstart = (ch != 3 && (a.tri & 2)) ? q1 : 0;
+        for (int cb = qstart; cb < N; cb += pm_list ? kTriChunk : N) {
+          int cnt = N - cb;
+          if (pm_list) {
+            constexpr int kPer = kTriChunk / kTileQ;
+            const int ce = min(N, cb + kTriChunk), lo = cb + threadIdx.x * kPer;
+            unsigned fl = 0;
+            int nf = 0;
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int q2 = lo + i;
+                if (q2 < ce) {
+                    const int4 c2 = t.qc[q2];
+                    const int q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
+                                                t.mesh[0], t.mesh[1], t.mesh[2]);
+                    if (q2 <= q3) { fl |= 1u << i; ++nf; }
+                }
+            }
+            int off = block_exclusive_scan(nf, s_scan, &cnt);
+#pragma unroll
+            for (int i = 0; i < kPer; ++i)
+                if ((fl >> i) & 1u) s_tri[off++] = (unsigned short)(threadIdx.x * kPer + i);
+            __syncthreads();
+          }
+          for (int qb = 0; qb < cnt; qb += kTileQ * kQPT) {
             // window: this thread's q'' of the round (up to kQPT) against every partner branch j'
             int n_ent = 0;
             unsigned long long ent[NB * kQPT];
-            for (int q2 = qb + threadIdx.x; q2 < min(N, qb + kTileQ * kQPT); q2 += kTileQ) {
+            for (int ix = qb + threadIdx.x; ix < min(cnt, qb + kTileQ * kQPT); ix += kTileQ) {
+                const int q2 = cb + (pm_list ? (int)s_tri[ix] : ix);
                 const int4 c2 = t.qc[q2];
                 const int q3 = q_index_near(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                             t.mesh[0], t.mesh[1], t.mesh[2]);
@@ -209,7 +239,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                                         << (NB * j3);
                         kept &= okj;
                         if (kept)
-                            ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
+                            ent[n_ent++] = ((unsigned long long)(ix - qb) << 48) |
                                            ((unsigned long long)j1 << 40) | tri_bits | kept;
                         continue;
                     }
@@ -243,7 +273,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                             sure |= 1ull << k;
                     }
                     if (sure)
-                        ent[n_ent++] = ((unsigned long long)(q2 - qb) << 48) |
+                        ent[n_ent++] = ((unsigned long long)(ix - qb) << 48) |
                                        ((unsigned long long)j1 << 40) | tri_bits | sure;
                 }
             }
@@ -255,7 +285,8 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
             for (int it = threadIdx.x; it < total; it += kTileQ) {
                 ++acc_ent;
                 const unsigned long long e = sQ[it];
-                const int iq2 = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
+                const int ixe = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
+                const int iq2 = cb + (pm_list ? (int)s_tri[ixe] : ixe);
                 const int tri = (int)((e >> 36) & 3u);
                 const int4 cc2 = t.qc[iq2];
                 const int iq3 = q_index_near(b0 + s2 * cc2.x, b1 + s2 * cc2.y, b2 + s2 * cc2.z,
@@ -378,6 +409,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 }
             }
             __syncthreads();                                     // sQ reused by the next round
+          }
         }
     }
     double sums[2] = {acc_g.value(), acc_wp.value()};

@@ -158,8 +158,7 @@ def clocks_stop(p, f, gpu_index):
 # kernel, from one ncu capture of the same kernel on the 6x6x6 seed-0 crystal (279,936 units per
 # launch); key (mixed precision, channel, branches).  The bytes are the per-unit W reads, so they
 # scale with the unit count.
-TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.135276e9 + 67.030784e6) / 279936,
-                    (True, "4ph++", 6): (4.124877e9 + 44.873984e6) / 279936}
+TRAFFIC_PER_UNIT = {(True, "4ph+-", 6): (4.109239e9 + 19.932e6) / 279936}
 
 
 def flops_alg(stats, info, nb):

@@ -2,8 +2,9 @@
 // contraction X = Σ_r P_r^s2 W_r on the tensor cores (tcgen05).
 //
 // Persistent CTAs of 384 threads (one per SM: they hold all 512 TMEM columns) loop over units
-// (λ, q').  For a round of 128 partner points q'' the contraction of every (c, d) key group is one
-// real matrix product covering all partner branches j':
+// (λ, q').  On the triangular domain a unit first lists its q'' <= q''' (block scan, ascending);
+// the rounds then run over that list.  For a round of 128 partner points q'' the contraction of
+// every (c, d) key group is one real matrix product covering all partner branches j':
 //   [Xr | Xi](q'', j' γδ) = [Pr | s2 Pi](q'', r) . [[Wr, Wi], [-Wi, Wr]](r, j' γδ)
 // (rows q'' = MMA M = 128 = TMEM lanes; K = 2 x keys of the group, padded to 16; N = 112 columns
 // of which 108 hold the 6 x 9 complex (j', γδ)).  Operands are FP16 hi/lo splits (W scaled by a
@@ -12,8 +13,8 @@
 // contraction.  B is built once per unit, A once per round; one thread issues tcgen05.mma
 // (kind::f16) and tcgen05.commit to an mbarrier.  The three warpgroups then share the 128 rows:
 // warpgroup g reads X of partner branches j' = g and g + 3 for its row with tcgen05.ld and
-// evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights),
-// on the triangular domain of the channel when Φ4 allows it (one row of each swapped pair).
+// evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights:
+// 2 for a swapped pair, 1 on the diagonal q'' = q''' with j'' = j''').
 //
 // Waits on the mbarrier are bounded (fc4_options.timeout_cycles SM clocks, default 2e9); on expiry
 // the kernel sets the context's error flag (the reduction then writes NaN into Γ), waits once

@@ -2,10 +2,10 @@
 //
 // w4_kernel writes W_r[γδ](λ, q', j') for every partner branch j' of a unit (λ, q') to a global
 // buffer (HBM is otherwise idle here; one pass over the clusters per unit).  rates4_tile_kernel
-// then owns the unit: it copies that W to shared memory, sweeps q'' in rounds of 128 (one per
-// thread), tests the window against every j' at once (branch-free FP32 prefilter, rare
-// ambiguous candidates decided by the exact FP64 Δ), compacts the (q'', j', masks) entries with
-// a block scan, and evaluates them:
+// then owns the unit: it copies that W to shared memory, sweeps q'' in rounds of 128 threads x
+// kQPT q'' (over the unit's triangle where the partner-swap symmetry holds), tests the window
+// against every j' at once (branch-free FP32 prefilter, rare ambiguous candidates decided by the
+// exact FP64 Δ), compacts the (q'', j', masks) entries with a block scan, and evaluates them:
 //   FP32: X[c,d][γδ] = Σ_{r in (c,d)} P_r^s2 W_r[γδ] once per entry, Y = X e*''' per j''' (36 MACs);
 //   FP64: Y[cγ] = Σ_r P_r^s2 Σ_δ W_r[γδ] e*'''(dδ) per j''' (register-light).
 // The same window decision, weights and accumulation as the general kernel (k_rates4.cuh).

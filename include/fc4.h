@@ -239,8 +239,54 @@ fc4_status fc4_check_device(fc4_ctx *ctx);
 /* fc4_info - sizes of a context: out[0..7] = n_atoms, nb, N, nc2, nc3, nc4, n_keys, precision. */
 fc4_status fc4_info(const fc4_ctx *ctx, long long out[8]);
 
-/* fc4_last_error - message of the last failed call on ctx (or of the last failed fc4_init when
- * ctx is NULL).  The string lives until the next call on ctx. */
+/* ---------------------------------------------------------------- irreducible q-points
+ * The mode loops of Algorithms 1 and 3-5 run over N_bands x N_list modes, N_list being the
+ * irreducible q-points of the mesh.  A space-group operation of the crystal that also maps its
+ * force constants onto themselves permutes the partner q-points of the mesh and keeps
+ * frequencies, occupations and |V|², so Γ(S q, j) = Γ(q, j) in every channel; q -> -q (real
+ * force constants) does the same.  These three host-only calls (no context, no GPU; errors in
+ * fc4_last_error(NULL)) find the operations, the irreducible points, and spread the rates that
+ * fc4_rates computes on those points (q_subset) over the whole mesh for fc4_kappa.  Exact for
+ * a fixed σ only: the adaptive width σ = s sqrt(Σ_k ((Δv . b_k) / n_k)² / 6) takes its Δv from
+ * Hellmann-Feynman velocities, which inside a degenerate subspace depend on the eigenvector basis
+ * chosen at each q, so Γ with that width is not constant on a star. */
+
+/* fc4_symmetry_ops - the space-group operations {W | w} of a primitive cell, in fractional
+ * coordinates f -> W f + w (W integer with entries in {-1, 0, 1}, det W = ±1, W^T G W = G for the
+ * metric G_ij = a_i . a_j; w in [0, 1)).  An operation is returned when it maps every atom onto
+ * an atom of the same mass (within 1e-6 of the longest lattice vector) and every cluster of
+ * phi2, phi3 and phi4 (each may be NULL or empty) onto a stored cluster with the tensor rotated,
+ * Φ'[α'β'..] = Σ S_α'α S_β'β .. Φ[αβ..] with S = A^T W A^-T, within tol x max |Φ| of that order
+ * (tol <= 0: 1e-8); a cluster whose image is not stored must rotate to below that bound.
+ * Layouts as for fc4_init.  rot: host [max_ops][3][3] row-major W; trans: host [max_ops][3] w;
+ * *n_ops receives the number of operations.  Returns FC4_ERR_INVALID (with *n_ops set) when
+ * more than max_ops are found; max_ops = 0 with NULL rot/trans only counts them. */
+fc4_status fc4_symmetry_ops(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_ifc *phi3,
+                            const fc4_ifc *phi4, double tol, int max_ops, int *rot, double *trans,
+                            int *n_ops);
+
+/* fc4_irreducible_q - orbits of the mesh q-points under the group generated by the operations
+ * W (rot: host [n_ops][3][3], as from fc4_symmetry_ops) and, with flags bit 0, time reversal
+ * q -> -q.  A q in reciprocal fractional coordinates maps as k' = W^-T k; an operation that
+ * does not map the mesh onto itself is ignored.  rep: host [N] receives for every q the
+ * smallest q index of its orbit (rep[q] == q marks an irreducible point); *n_irr the number of
+ * orbits.  FC4_ERR_INVALID for det W != ±1 or any other flag bit. */
+fc4_status fc4_irreducible_q(const int mesh[3], int n_ops, const int *rot, int flags, int *rep,
+                             int *n_irr);
+
+/* fc4_expand_irreducible - per-mode values of the whole mesh from those of its irreducible
+ * points: full[s][q nb + j] = the mean of sub[s][p nb + j'] over the branches j' degenerate with
+ * j at the representative r = rep[q] (|ω difference| <= deg_tol between neighbours in ascending
+ * ω), p = the position of r among the irreducible points in ascending order.  Averaging over a
+ * degenerate group makes the result independent of the eigenvector basis chosen inside it (the
+ * group's sum is invariant; its members are not).  rep: host [N] as from fc4_irreducible_q;
+ * omega: host [N nb] rad/ps; sub: host [n_sets][n_irr nb] (e.g. Γ, WP of fc4_rates on the
+ * irreducible points, copied to the host); full: host [n_sets][N nb]. */
+fc4_status fc4_expand_irreducible(const int mesh[3], int nb, const int *rep, const double *omega,
+                                  double deg_tol, int n_sets, const double *sub, double *full);
+
+/* fc4_last_error - message of the last failed call on ctx (or, when ctx is NULL, of the last
+ * failed fc4_init or host-only call).  The string lives until the next call on ctx. */
 const char *fc4_last_error(const fc4_ctx *ctx);
 
 /* fc4_destroy - free every device and host resource of ctx (NULL is a no-op). */

@@ -80,6 +80,10 @@ def load(build_if_missing: bool = False):
         "fc4_set_block_threads": [vp, i],
         "fc4_set_tensor_cores": [vp, i],
         "fc4_check_device": [vp],
+        "fc4_symmetry_ops": [ctypes.POINTER(_Crystal), ctypes.POINTER(_IFC), ctypes.POINTER(_IFC),
+                             ctypes.POINTER(_IFC), d, i, vp, vp, vp],
+        "fc4_irreducible_q": [vp, i, vp, i, vp, vp],
+        "fc4_expand_irreducible": [vp, i, vp, vp, d, i, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -111,6 +115,35 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _structs(crystal, phi2, phi3, phi4, keep: list):
+    """fc4_crystal and the three fc4_ifc of a crystal and its clusters; ``keep`` holds the
+    arrays they point into."""
+    def arr(x, dt):
+        a = _np(x, dt)
+        keep.append(a)
+        return a
+
+    c = _Crystal()
+    c.n_atoms = int(np.asarray(crystal.masses).size)
+    c.lattice = (ctypes.c_double * 9)(*_np(crystal.lattice, np.float64).reshape(-1))
+    c.positions = _ptr(arr(crystal.positions, np.float64))
+    c.masses = _ptr(arr(crystal.masses, np.float64))
+
+    def ifc(f, order):
+        s = _IFC()
+        s.order = order
+        if f is None:
+            s.n_clusters = 0
+            return s
+        s.n_clusters = int(np.asarray(f.atoms).shape[0])
+        s.atoms = _ptr(arr(f.atoms, np.int32))
+        s.cells = _ptr(arr(f.cells, np.int32))
+        s.phi = _ptr(arr(f.phi, np.float64))
+        return s
+
+    return c, ifc(phi2, 2), ifc(phi3, 3), ifc(phi4, 4)
+
+
 class Engine:
     """One fc4 context: a crystal, its Φ2/Φ3/Φ4 clusters and a Γ-centred mesh on the device.
 
@@ -127,31 +160,7 @@ class Engine:
         self.n_atoms = int(np.asarray(crystal.masses).size)
         self.nb = 3 * self.n_atoms
         keep = []
-
-        def arr(x, dt):
-            a = _np(x, dt)
-            keep.append(a)
-            return a
-
-        c = _Crystal()
-        c.n_atoms = self.n_atoms
-        c.lattice = (ctypes.c_double * 9)(*_np(crystal.lattice, np.float64).reshape(-1))
-        c.positions = _ptr(arr(crystal.positions, np.float64))
-        c.masses = _ptr(arr(crystal.masses, np.float64))
-
-        def ifc(f, order):
-            s = _IFC()
-            s.order = order
-            if f is None:
-                s.n_clusters = 0
-                return s
-            s.n_clusters = int(np.asarray(f.atoms).shape[0])
-            s.atoms = _ptr(arr(f.atoms, np.int32))
-            s.cells = _ptr(arr(f.cells, np.int32))
-            s.phi = _ptr(arr(f.phi, np.float64))
-            return s
-
-        i2, i3, i4 = ifc(phi2, 2), ifc(phi3, 3), ifc(phi4, 4)
+        c, i2, i3, i4 = _structs(crystal, phi2, phi3, phi4, keep)
         self.nc3 = i3.n_clusters
         self.nc4 = i4.n_clusters
         opt = _Options()

@@ -41,6 +41,8 @@ thread_local std::string g_init_error;
 
 }  // namespace
 
+void fc4::set_host_error(const char *msg) { g_init_error = msg; }
+
 struct fc4_ctx {
     fc4::Tables t{};
     int nc2 = 0, nc3 = 0, nc4 = 0;

@@ -119,6 +119,9 @@ cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *
                                float *invw32, float4 *vp32, float4 *vp32lo, cudaStream_t s);
 cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ, float *occ32,
                                cudaStream_t s);
+// message returned by fc4_last_error(NULL) (errors of calls without a context)
+void set_host_error(const char *msg);
+
 cudaError_t launch_phase_tables(const Tables &t, const int4 *key_r, double2 *P4, float2 *P4_32,
                                 cudaStream_t s);
 cudaError_t launch_kappa(const Tables &t, double hbar_over_kT, double kB, const double *gamma,

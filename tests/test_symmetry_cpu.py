@@ -225,3 +225,39 @@ def test_adaptive_width_is_not_star_invariant(clean, ops):
         v = degenerate_mean(g.sum(0), P.modes.omega[modes], nb).reshape(star.size, nb)
         worst = max(worst, float(np.max(np.abs(v - v[0]) / np.maximum(np.abs(v[0]), 1e-12))))
     assert worst > 1e-3
+
+
+def _batch_system(seed):
+    from synth.morse import batch_crystal, morse_ifcs
+    c, _ = batch_crystal(seed)
+    return (c,) + tuple(morse_ifcs(c, None, seed=seed, perturb=0.0))
+
+
+def test_zincblende_point_group():
+    """Two unequal masses on the diamond sites: the 24 operations of -43m; with q -> -q the
+    fcc 4x4x4 mesh again has 8 irreducible points (10 without)."""
+    sysz = _batch_system(0)
+    rot, trans = S.symmetry_ops(*sysz)
+    assert len(rot) == 24
+    assert np.allclose(trans, 0.0)                           # no operation swaps the two sites
+    assert S.irreducible_q((4, 4, 4), rot)[1].size == 8
+    assert S.irreducible_q((4, 4, 4), rot, time_reversal=False)[1].size == 10
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gamma_constant_on_every_star_of_a_small_mesh(seed):
+    """Zincblende (24 operations) and a four-atom 1x1x2 supercell with four masses (2
+    operations): the oracle's 3ph rates on every q of the 3x3x3 mesh are constant on each star
+    of the library's orbits (with q -> -q)."""
+    sysb = _batch_system(seed)
+    rot, _ = S.symmetry_ops(*sysb)
+    mesh = (3, 3, 3)
+    P = oracle.Problem(*sysb, mesh)
+    nb = P.nb
+    rep, irr = S.irreducible_q(mesh, rot)
+    assert irr.size < 27
+    g, _, _ = P.rates(None, channel_mask=3)
+    for ch in (0, 1):
+        v = degenerate_mean(g[ch], P.modes.omega, nb).reshape(27, nb)
+        ref = v[rep]
+        assert np.allclose(v, ref, rtol=1e-10, atol=1e-14 * np.abs(v).max())

@@ -338,6 +338,65 @@ def test_weighted_phase_space_3ph_brute_force(prob3):
         assert abs(wp[0, i] - tot / N) < 1e-12 * abs(tot / N)
 
 
+@pytest.mark.parametrize("ch", [2, 3, 4])
+def test_weighted_phase_space_4ph_brute_force(prob3, ch):
+    """WP4 = (1/N²) Σ c_s F_s g(Δ) / (ω ω1 ω2 ω3) over every candidate (q1, j1, q2, j2, j3) of the
+    rectangular partner domain with |Δ| <= 2σ, written out with numpy: c = ½, ½, ⅙ for ++, +-,
+    --; F the forward-minus-backward occupation products; the three acoustic modes at Γ excluded
+    as partners.  The kept counts match too."""
+    P = prob3
+    nb, N = P.nb, P.nq
+    s1, s2 = {2: (1, 1), 3: (1, -1), 4: (-1, -1)}[ch]
+    c_s = {2: 0.5, 3: 0.5, 4: 1.0 / 6.0}[ch]
+    w = P.modes.omega.reshape(N, nb)
+    n = oracle.occupations(P.modes.omega, P.T).reshape(N, nb)
+    ok = np.ones((N, nb), bool)
+    ok[0, :3] = False
+    sig = P.sigma * oracle.SIGMA_THZ_TO_RADPS
+    qc = oracle.q_coords(P.mesh)
+    mesh = np.asarray(P.mesh)
+    modes = [m for m in range(3, N * nb) if P.processes(ch, m).size > 0][:3]
+    assert len(modes) == 3
+    _, wp, cnt = P.rates(modes, channel_mask=1 << ch)
+    for i, m0 in enumerate(modes):
+        q0, j0 = divmod(m0, nb)
+        w0 = w[q0, j0]
+        tot, kept = 0.0, 0
+        for q1 in range(N):
+            for q2 in range(N):
+                c3 = (qc[q0] + s1 * qc[q1] + s2 * qc[q2]) % mesh
+                q3 = int(c3[0] + mesh[0] * (c3[1] + mesh[1] * c3[2]))
+                a = w[q1][:, None, None]
+                b = w[q2][None, :, None]
+                c = w[q3][None, None, :]
+                if ch == 2:
+                    d = (w0 - c) + (a + b)
+                elif ch == 3:
+                    d = (w0 + a) - (b + c)
+                else:
+                    srt = np.sort(np.stack(np.broadcast_arrays(a, b, c)), axis=0)
+                    d = w0 - ((srt[0] + srt[1]) + srt[2])
+                m = (np.abs(d) <= 2.0 * sig) & ok[q1][:, None, None] & ok[q2][None, :, None] & ok[q3][None, None, :]
+                if not m.any():
+                    continue
+                n1 = n[q1][:, None, None]
+                n2 = n[q2][None, :, None]
+                n3 = n[q3][None, None, :]
+                if ch == 2:
+                    F = n1 * n2 * (1 + n3) - (1 + n1) * (1 + n2) * n3
+                elif ch == 3:
+                    F = n1 * (1 + n2) * (1 + n3) - (1 + n1) * n2 * n3
+                else:
+                    F = (1 + n1) * (1 + n2) * (1 + n3) - n1 * n2 * n3
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    term = c_s * F * np.exp(-d * d / sig ** 2) / (sig * math.sqrt(math.pi) * w0 * a * b * c)
+                tot += float(term[m].sum())
+                kept += int(m.sum())
+        assert cnt[ch, i] == kept
+        assert kept > 0
+        assert abs(wp[ch, i] - tot / N ** 2) < 1e-11 * abs(tot / N ** 2)
+
+
 # ------------------------------------------------------------------------------ rates
 
 def test_band_folding_equivalence():

@@ -455,6 +455,24 @@ def test_kappa_isotropic_unperturbed(sys_clean):
     assert np.abs(k - np.diag(np.diag(k))).max() < 1e-6 * k[0, 0]
 
 
+def test_kappa_classical_limit(sys0):
+    """At T = 1e8 K every mode carries k_B (x = ħω/k_B T ~ 1e-5, C/k_B = 1 - x²/12 + ...), so with
+    Γ = 1 ps⁻¹ on every mode κ = k_B Σ v⊗v τ / (N V).  In Å, ps and Å³ the unit chain collapses to
+    one factor, k_B [J/K] x 10⁴ (Å²/ps² -> m²/s²) x 10⁻¹² (ps) / 10⁻³⁰ (Å³) = 1.380649e-23 x 10²²."""
+    c, p2, _, _ = sys0
+    mesh = (3, 3, 3)
+    m = oracle.harmonic(c, p2, mesh)
+    g = np.ones_like(m.omega)
+    k = oracle.kappa(c, m, 1e8, g, mesh)
+    on = m.omega > 0
+    v = m.vel[on]
+    vol = abs(np.linalg.det(np.asarray(c.lattice)))
+    ref = 1.380649e-23 * 1e22 * (v.T @ v) / (27 * vol)
+    assert np.allclose(k, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    k2 = oracle.kappa(c, m, 1e8, 2.0 * g, mesh)                  # τ = 1/Γ
+    assert np.allclose(k2, 0.5 * k, rtol=1e-14)
+
+
 # ------------------------------------------------------------------------------ gradient
 
 @pytest.fixture(scope="module")

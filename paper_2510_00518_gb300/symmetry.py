@@ -53,7 +53,8 @@ def irreducible_q(mesh, rot, time_reversal: bool = True):
     _check(lib, lib.fc4_irreducible_q(_ptr(m), r.shape[0], _ptr(r) if r.size else None, flags,
                                       _ptr(rep), ctypes.cast(ctypes.pointer(n), ctypes.c_void_p)))
     irr = np.flatnonzero(rep == np.arange(N)).astype(np.int32)
-    assert irr.size == n.value
+    if irr.size != n.value:
+        raise FC4Error(1, f"fc4_irreducible_q: {n.value} orbits reported, {irr.size} representatives")
     return rep, irr
 
 

@@ -518,6 +518,62 @@ def test_gradient_central_differences(prob2):
         assert abs(fd - an) < 1e-7 * max(abs(an), 1e-3 * gref), (order, c, k, fd, an)
 
 
+def _weight(ch, w0, ws, ns, sig):
+    """c_s F_s g(Δ) / Π ω of one process, written out (Δ in the canonical parenthesisation)."""
+    g = lambda d: math.exp(-d * d / sig ** 2) / (sig * math.sqrt(math.pi))
+    if ch == 0:
+        (a, b), (n1, n2) = ws, ns
+        return (n1 - n2) * g((w0 + a) - b) / (w0 * a * b)
+    if ch == 1:
+        (a, b), (n1, n2) = ws, ns
+        return 0.5 * (1 + n1 + n2) * g(w0 - (a + b)) / (w0 * a * b)
+    (a, b, c), (n1, n2, n3) = ws, ns
+    if ch == 2:
+        return 0.5 * (n1 * n2 * (1 + n3) - (1 + n1) * (1 + n2) * n3) * g((w0 - c) + (a + b)) / (w0 * a * b * c)
+    if ch == 3:
+        return 0.5 * (n1 * (1 + n2) * (1 + n3) - (1 + n1) * n2 * n3) * g((w0 + a) - (b + c)) / (w0 * a * b * c)
+    s = sorted((a, b, c))
+    return ((1 + n1) * (1 + n2) * (1 + n3) - n1 * n2 * n3) / 6.0 * g(w0 - ((s[0] + s[1]) + s[2])) / (w0 * a * b * c)
+
+
+@pytest.mark.parametrize("ch", [0, 1, 2, 3, 4])
+def test_gamma_assembled_from_matrix_elements(prob3, ch):
+    """Γ = C/N^k Σ_kept w |V|² rebuilt term by term from the oracle's kept list, its matrix
+    elements (pinned by supercell finite differences) and the weights written out here, on the
+    3x3x3 mesh; C3, C4 from the two-route unit derivation."""
+    P = prob3
+    nb, N = P.nb, P.nq
+    qc = oracle.q_coords(P.mesh)
+    mesh = np.asarray(P.mesh)
+    w = P.modes.omega
+    n = oracle.occupations(w, P.T)
+    sig = P.sigma * oracle.SIGMA_THZ_TO_RADPS
+    modes = [m for m in range(3, N * nb) if P.processes(ch, m).size > 0][:2]
+    assert len(modes) == 2
+    g, _, _ = P.rates(modes, channel_mask=1 << ch)
+    idx = lambda c: int(c[0] + mesh[0] * (c[1] + mesh[1] * c[2]))
+    for i, m0 in enumerate(modes):
+        q0 = m0 // nb
+        tot = 0.0
+        for wd in P.processes(ch, m0).tolist():
+            if ch < 2:
+                q1, j1, j2 = oracle.decode3(wd, nb)
+                s = 1 if ch == 0 else -1
+                m1 = q1 * nb + j1
+                m2 = idx((qc[q0] + s * qc[q1]) % mesh) * nb + j2
+                V = P.v3(s, m0, m1, m2)
+                tot += _weight(ch, w[m0], (w[m1], w[m2]), (n[m1], n[m2]), sig) * abs(V) ** 2
+            else:
+                q1, j1, q2, j2, j3 = oracle.decode4(wd, nb, N)
+                s1, s2 = {2: (1, 1), 3: (1, -1), 4: (-1, -1)}[ch]
+                m1, m2 = q1 * nb + j1, q2 * nb + j2
+                m3 = idx((qc[q0] + s1 * qc[q1] + s2 * qc[q2]) % mesh) * nb + j3
+                V = P.v4(s1, s2, m0, m1, m2, m3)
+                tot += _weight(ch, w[m0], (w[m1], w[m2], w[m3]), (n[m1], n[m2], n[m3]), sig) * abs(V) ** 2
+        ref = (oracle.C3 / N if ch < 2 else oracle.C4 / N ** 2) * tot
+        assert abs(g[ch, i] - ref) <= 1e-11 * abs(ref) + 1e-300
+
+
 def test_gamma_scales_quadratically(prob2):
     modes = [5, 30]
     g, _, _ = prob2.rates(modes)

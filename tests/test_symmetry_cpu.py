@@ -25,6 +25,12 @@ from synth import morse_system
 S = pytest.importorskip("paper_2510_00518_gb300.symmetry")
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_2510_00518_gb300 import build as fc4_build
+    fc4_build.build()                      # host-only calls: the library must exist, no GPU needed
+
+
 @pytest.fixture(scope="module")
 def clean():
     return morse_system(seed=0, perturb=0.0)

@@ -4,7 +4,8 @@ Under the relaxation-time approximation every mode's Γ is independent (paper, I
 the q points are split into contiguous blocks, one per rank, with no exchange while the rates
 are computed.  κ is a sum over modes: each rank evaluates the contribution of its own modes
 (the Γ of all other modes set to 0, which fc4_kappa skips) and one all-reduce of 9 doubles
-assembles the total."""
+assembles the total.  With irreducible q-points the representatives are split the same way
+and each rank spreads its own over their stars before its κ contribution."""
 from __future__ import annotations
 
 import numpy as np
@@ -41,3 +42,29 @@ def sharded_rates_kappa(engine, T: float, sigma_thz: float, channel_mask: int = 
         full[:, int(qs[0]) * engine.nb:(int(qs[-1]) + 1) * engine.nb] = g
     kap = engine.kappa(T, full, channel_mask).reshape(-1).clone()
     return qs, g, allreduce_kappa(kap, group).view(3, 3)
+
+
+def sharded_rates_kappa_irreducible(engine, T: float, sigma_thz: float, rot=None,
+                                    channel_mask: int = 31, time_reversal: bool = True,
+                                    deg_tol: float = 1e-5, group=None):
+    """The irreducible q-points split into contiguous blocks over the ranks: each rank computes
+    the rates of its block (fixed σ), spreads them over the stars it owns (the other stars stay
+    0 and fc4_kappa skips them) and adds its κ contribution in one all-reduce of 9 doubles.
+    Returns (this rank's irreducible q, their Γ [5, n*nb], the total κ)."""
+    import torch
+    import torch.distributed as dist
+    from .symmetry import expand_irreducible, irreducible_q
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    rank = dist.get_rank(group) if dist.is_initialized() else 0
+    r = np.zeros((0, 3, 3), np.int32) if rot is None else rot
+    rep, irr = irreducible_q(engine.mesh, r, time_reversal)
+    pos = shard_q(irr.size, rank, world)
+    mine = irr[pos]
+    g, _, _ = engine.rates(T, sigma_thz, channel_mask, q_subset=mine)
+    nb = engine.nb
+    sub = np.zeros((5, irr.size * nb))
+    if pos.size:
+        sub[:, int(pos[0]) * nb:(int(pos[-1]) + 1) * nb] = g.cpu().numpy()
+    full = expand_irreducible(engine.mesh, nb, rep, engine.get_modes()[0], sub, deg_tol)
+    kap = engine.kappa(T, torch.from_numpy(full).to(g.device), channel_mask).reshape(-1).clone()
+    return mine, g, allreduce_kappa(kap, group).view(3, 3)

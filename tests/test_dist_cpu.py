@@ -66,3 +66,64 @@ def test_two_rank_kappa_allreduce(tmp_path):
     for r in range(world):
         k = np.load(tmp_path / f"k{r}.npy")
         assert np.allclose(k, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+class _OracleEngine:
+    """The calls sharded_rates_kappa_irreducible makes on an Engine, answered by the oracle."""
+
+    def __init__(self, P):
+        self.P, self.mesh, self.nq, self.nb = P, P.mesh, P.nq, P.nb
+
+    def rates(self, T, sigma_thz, channel_mask, q_subset=None):
+        qs = np.arange(self.nq) if q_subset is None else np.asarray(q_subset)
+        modes = (qs[:, None] * self.nb + np.arange(self.nb)).reshape(-1).astype(np.int32)
+        g, wp, cnt = self.P.rates(modes, channel_mask=channel_mask)
+        return torch.from_numpy(g), torch.from_numpy(wp), torch.from_numpy(cnt)
+
+    def get_modes(self):
+        return self.P.modes.omega, self.P.modes.vel, self.P.modes.evec
+
+    def kappa(self, T, gamma, channel_mask):
+        g = gamma.numpy()
+        tot = sum(g[ch] for ch in range(5) if channel_mask >> ch & 1)
+        return torch.from_numpy(self.P.kappa(tot).reshape(-1))
+
+
+def _worker_irreducible(rank, world, port, out_dir):
+    import oracle
+    from synth import morse_system
+    from paper_2510_00518_gb300.dist import sharded_rates_kappa_irreducible
+    from paper_2510_00518_gb300.symmetry import symmetry_ops
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sysm = morse_system(seed=0, perturb=0.0)
+        rot, _ = symmetry_ops(*sysm)
+        eng = _OracleEngine(oracle.Problem(*sysm, (4, 4, 4)))
+        mine, g, k = sharded_rates_kappa_irreducible(eng, 300.0, 0.1, rot, channel_mask=0b11)
+        np.save(os.path.join(out_dir, f"irr{rank}.npy"), mine)
+        np.save(os.path.join(out_dir, f"ki{rank}.npy"), k.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_irreducible_kappa(tmp_path):
+    """The 8 irreducible points of the symmetric 4x4x4 mesh split over two ranks: disjoint blocks
+    covering them all, and the all-reduced κ equals the oracle's full-mesh κ."""
+    import oracle
+    from synth import morse_system
+    from paper_2510_00518_gb300 import build as fc4_build
+    fc4_build.build()
+    world = 2
+    mp.start_processes(_worker_irreducible, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    mine = [np.load(tmp_path / f"irr{r}.npy") for r in range(world)]
+    allq = np.concatenate(mine)
+    assert allq.size == 8 and np.unique(allq).size == 8
+    P = oracle.Problem(*morse_system(seed=0, perturb=0.0), (4, 4, 4))
+    g, _, _ = P.rates(channel_mask=0b11)
+    ref = P.kappa(g.sum(0)).reshape(-1)
+    for r in range(world):
+        k = np.load(tmp_path / f"ki{r}.npy").reshape(-1)
+        assert np.allclose(k, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())

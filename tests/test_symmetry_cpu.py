@@ -205,8 +205,13 @@ def test_expanded_rates_and_kappa_equal_the_full_mesh(clean, ops):
     assert np.allclose(k_ex, k_full, rtol=1e-9, atol=1e-12 * np.abs(k_full).max())
 
 
-def test_host_calls_reject_bad_input(ops):
+def test_host_calls_reject_bad_input(clean, ops):
     lib = S.load()
+    with pytest.raises(S.FC4Error):
+        S.symmetry_ops(*clean, max_ops=4)               # 48 found
+    assert "48 operations found" in lib.fc4_last_error(None).decode()
+    with pytest.raises(S.FC4Error):
+        S.irreducible_q((4, 4, 0), ops[0])
     with pytest.raises(S.FC4Error):
         S.irreducible_q((4, 4, 4), np.array([[[2, 0, 0], [0, 1, 0], [0, 0, 1]]], np.int32))
     rep = np.arange(8, dtype=np.int32)

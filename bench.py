@@ -59,6 +59,8 @@ def parse():
                    help="one untimed fc4_rates call (for profilers): --mesh, --precision, --mask")
     p.add_argument("--mask", type=int, default=31, help="channel mask of --once")
     p.add_argument("--tc", action="store_true", help="--once with the tensor-core +- contraction")
+    p.add_argument("--cpu-sample", action="store_true",
+                   help="only the oracle sample (--cpu-q, --cpu-qp) on the host, one JSON line")
     return p.parse_args()
 
 
@@ -99,6 +101,38 @@ def cpu_oracle_sample(args, seed=0, qp=None, nq=None):
             f"4ph channels, partners q' < {qp} of {int(np.prod(mesh))}; {kept} kept processes")
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return kept, dt, desc, threads
+
+
+def cpu_host_info():
+    """(CPU model, logical cores) of the host, best effort."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
+
+
+def cpu_oracle_one_core(args):
+    """The oracle sample on one thread (a child process with OMP_NUM_THREADS=1), 6 modes and a
+    quarter of the partners q'; None if the child fails."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--cpu-q", "1",
+           "--cpu-qp", str(max(2, args.cpu_qp // 4)), "--mesh", str(args.mesh), "--T", str(args.T),
+           "--sigma", str(args.sigma)]
+    try:
+        r = subprocess.run(cmd, env=dict(os.environ, OMP_NUM_THREADS="1"), capture_output=True,
+                           text=True, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except Exception:
+        return None
 
 
 def clocks_start():
@@ -383,8 +417,10 @@ def run_gpu(args):
 
     if rank == 0 and world == 1 and not args.no_cpu:
         kept, dt, desc, thr = cpu_oracle_sample(args)
+        model, ncpu = cpu_host_info()
         result["cpu_baseline"] = {"value": kept / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                  "sample": desc, "seconds": dt}
+                                  "sample": desc, "seconds": dt, "cpu_model": model, "nproc": ncpu,
+                                  "one_core": cpu_oracle_one_core(args)}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -411,7 +447,8 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Morse diamond crystal)",
            "config": config_of(args, "fp64-oracle"),
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+                            "cpu_model": cpu_host_info()[0], "nproc": cpu_host_info()[1]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -471,7 +508,10 @@ def run_once(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.once:
+    if a.cpu_sample:
+        kept, dt, desc, thr = cpu_oracle_sample(a)
+        print(json.dumps({"value": kept / dt, "unit": UNIT, "cores": thr, "seconds": dt, "sample": desc}))
+    elif a.once:
         run_once(a)
     elif a.batch:
         run_batch(a)

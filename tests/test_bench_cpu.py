@@ -25,5 +25,19 @@ def test_reference_arm_json_line():
     assert d["config"]["workload"] == "morse-diamond-2atom-8x8x8-all-modes"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert cb["cpu_model"] and cb["nproc"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_one_core_oracle_sample_and_host_info():
+    """The single-thread oracle figure the GPU arm adds to cpu_baseline (child process with
+    OMP_NUM_THREADS=1) and the host description."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    args = argparse.Namespace(cpu_qp=8, mesh=8, T=300.0, sigma=0.1)
+    d = bench.cpu_oracle_one_core(args)
+    assert d is not None and d["cores"] == 1 and d["value"] > 0 and "q' < 2" in d["sample"]
+    model, n = bench.cpu_host_info()
+    assert model and n >= 1

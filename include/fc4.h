@@ -259,8 +259,9 @@ fc4_status fc4_info(const fc4_ctx *ctx, long long out[8]);
  * Φ'[α'β'..] = Σ S_α'α S_β'β .. Φ[αβ..] with S = A^T W A^-T, within tol x max |Φ| of that order
  * (tol <= 0: 1e-8); a cluster whose image is not stored must rotate to below that bound.
  * Layouts as for fc4_init.  rot: host [max_ops][3][3] row-major W; trans: host [max_ops][3] w;
- * *n_ops receives the number of operations.  Returns FC4_ERR_INVALID (with *n_ops set) when
- * more than max_ops are found; max_ops = 0 with NULL rot/trans only counts them. */
+ * *n_ops receives the number of operations.  max_ops = 0 (rot and trans may be NULL) only
+ * counts them; with max_ops > 0, finding more than max_ops returns FC4_ERR_INVALID (with *n_ops
+ * set and the first max_ops written). */
 fc4_status fc4_symmetry_ops(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_ifc *phi3,
                             const fc4_ifc *phi4, double tol, int max_ops, int *rot, double *trans,
                             int *n_ops);

@@ -257,7 +257,7 @@ extern "C" fc4_status fc4_symmetry_ops(const fc4_crystal *crystal, const fc4_ifc
         }
     }
     *n_ops = count;
-    if (count > max_ops)
+    if (max_ops > 0 && count > max_ops)
         return fail(FC4_ERR_INVALID, "fc4_symmetry_ops: " + std::to_string(count) +
                                          " operations found, max_ops = " + std::to_string(max_ops));
     return FC4_OK;

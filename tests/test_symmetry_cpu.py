@@ -212,6 +212,14 @@ def test_host_calls_reject_bad_input(clean, ops):
     assert "48 operations found" in lib.fc4_last_error(None).decode()
     with pytest.raises(S.FC4Error):
         S.irreducible_q((4, 4, 0), ops[0])
+    import ctypes
+    from paper_2510_00518_gb300 import _structs
+    keep = []
+    c, i2, i3, i4 = _structs(*clean, keep)
+    n = ctypes.c_int(-1)
+    assert lib.fc4_symmetry_ops(ctypes.byref(c), ctypes.byref(i2), ctypes.byref(i3), ctypes.byref(i4),
+                                0.0, 0, None, None, ctypes.cast(ctypes.pointer(n), ctypes.c_void_p)) == 0
+    assert n.value == 48                                 # max_ops = 0: count only
     with pytest.raises(S.FC4Error):
         S.irreducible_q((4, 4, 4), np.array([[[2, 0, 0], [0, 1, 0], [0, 0, 1]]], np.int32))
     rep = np.arange(8, dtype=np.int32)

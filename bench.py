@@ -59,6 +59,9 @@ def parse():
                    help="one untimed fc4_rates call (for profilers): --mesh, --precision, --mask")
     p.add_argument("--mask", type=int, default=31, help="channel mask of --once")
     p.add_argument("--tc", action="store_true", help="--once with the tensor-core +- contraction")
+    p.add_argument("--irreducible", action="store_true",
+                   help="irreducible q-points against the full mesh (see run_irreducible)")
+    p.add_argument("--symmetric", action="store_true", help="--irreducible on the unperturbed crystal")
     p.add_argument("--cpu-sample", action="store_true",
                    help="only the oracle sample (--cpu-q, --cpu-qp) on the host, one JSON line")
     return p.parse_args()
@@ -493,6 +496,55 @@ def run_batch(args):
                       "kept_4ph_per_step": kept}))
 
 
+def run_irreducible(args):
+    """Rates of the whole mesh from its irreducible q-points (symmetry.rates_irreducible: fc4_rates
+    on one q per orbit, host spread over the stars) against the full-mesh step, both followed by
+    fc4_kappa, in one process.  ``--symmetric`` takes the unperturbed crystal (48 operations);
+    otherwise the bench crystal, whose only symmetry is q -> -q.  Prints one JSON line with both
+    step times (wall clock, synchronised, L2 flushed before each step) and the κ difference."""
+    import torch
+    from synth import morse_system
+    from paper_2510_00518_gb300 import Engine, FP64, MIXED
+    from paper_2510_00518_gb300.symmetry import rates_irreducible, symmetry_ops
+    torch.cuda.set_device(0)
+    sysm = morse_system(seed=0, perturb=0.0 if args.symmetric else 0.01)
+    mesh = (args.mesh,) * 3
+    rot, _ = symmetry_ops(*sysm)
+    eng = Engine(*sysm, mesh, precision=MIXED if args.precision == "mixed" else FP64)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        out, ts = None, []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        return out, float(np.mean(ts))
+
+    def full():
+        g, _, _ = eng.rates(args.T, args.sigma, 31)
+        return g, eng.kappa(args.T, g, 31)
+
+    def irreducible():
+        g, _, n = rates_irreducible(eng, args.T, args.sigma, 31, rot)
+        return g, eng.kappa(args.T, g, 31), n
+
+    (g_f, k_f), ms_f = timed(full)
+    (g_i, k_i, n_irr), ms_i = timed(irreducible)
+    kf, ki = k_f.cpu().numpy(), k_i.cpu().numpy()
+    print(json.dumps({"mode": "irreducible q-points", "crystal": "unperturbed (48 operations)" if args.symmetric
+                      else "bench crystal (q -> -q only)", "n_operations": int(len(rot)),
+                      "n_q": int(np.prod(mesh)), "n_irreducible": n_irr, "precision": args.precision,
+                      "ms_per_step_full": ms_f, "ms_per_step_irreducible": ms_i, "speedup": ms_f / ms_i,
+                      "kappa_rel_err": float(np.abs(ki - kf).max() / np.abs(kf).max()),
+                      "steps": args.steps, "warmup": args.warmup,
+                      "timing": "wall clock around synchronised calls; L2 flushed before each step"}))
+
+
 def run_once(args):
     """A single rates call on the workload (profiling helper, no timing, no JSON line)."""
     import torch
@@ -511,6 +563,8 @@ if __name__ == "__main__":
     if a.cpu_sample:
         kept, dt, desc, thr = cpu_oracle_sample(a)
         print(json.dumps({"value": kept / dt, "unit": UNIT, "cores": thr, "seconds": dt, "sample": desc}))
+    elif a.irreducible:
+        run_irreducible(a)
     elif a.once:
         run_once(a)
     elif a.batch:

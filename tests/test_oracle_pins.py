@@ -719,6 +719,38 @@ def test_enumeration_adaptive_matches_brute_force(sys0, mesh):
         assert total > 0
 
 
+def test_weighted_phase_space_4ph_adaptive(sys0):
+    """WP4+- with adaptive widths: (1/N²) Σ ½ F g(Δ, σ) / (ω ω1 ω2 ω3) over the oracle's kept list,
+    with σ = s sqrt(Δv^T G Δv / 6), Δv = v2 - v3 (the two legs the free partner sum moves
+    together), G = B^T diag(n^-2) B (the quadratic-form route), and the kept count."""
+    P = oracle.Problem(*sys0, (3, 3, 3), sigma=1.0, sigma_adaptive=True)
+    nb, N = P.nb, P.nq
+    occ = oracle.occupations(P.modes.omega, P.T)
+    w, v = P.modes.omega, P.modes.vel
+    B = oracle.reciprocal(P.crystal.lattice)
+    G = B.T @ np.diag(1.0 / np.asarray(P.mesh, float) ** 2) @ B
+    qc = oracle.q_coords(P.mesh)
+    modes = [m for m in range(3, N * nb) if P.processes(3, m).size > 0][:2]
+    assert len(modes) == 2
+    _, wp, cnt = P.rates(modes, channel_mask=8)
+    for i, m0 in enumerate(modes):
+        words = P.processes(3, m0)
+        assert cnt[3, i] == words.size
+        tot = 0.0
+        for wd in words.tolist():
+            q1, j1, q2, j2, j3 = oracle.decode4(wd, nb, N)
+            c3 = (qc[m0 // nb] + qc[q1] - qc[q2]) % 3
+            m1, m2 = q1 * nb + j1, q2 * nb + j2
+            m3 = int(c3[0] + 3 * (c3[1] + 3 * c3[2])) * nb + j3
+            dv = v[m2] - v[m3]
+            sg = math.sqrt(dv @ G @ dv / 6.0)
+            d = (w[m0] + w[m1]) - (w[m2] + w[m3])
+            n1, n2, n3 = occ[m1], occ[m2], occ[m3]
+            F = n1 * (1 + n2) * (1 + n3) - (1 + n1) * n2 * n3
+            tot += 0.5 * F * math.exp(-d * d / sg ** 2) / (sg * math.sqrt(math.pi) * w[m0] * w[m1] * w[m2] * w[m3])
+        assert abs(wp[3, i] - tot / N ** 2) < 1e-10 * abs(tot / N ** 2)
+
+
 def test_weighted_phase_space_adaptive_brute_force(sys0):
     """WP3- with adaptive widths: (1/N) Σ ½ (1 + n' + n'') g(Δ, σ_λ'λ'') / (ω ω' ω'') (the ½ counts
     each unordered partner pair once), with σ by the quadratic-form route, over the brute-force

@@ -197,6 +197,8 @@ class _Problem(ctypes.Structure):
         ("phi4", ctypes.c_void_p),
         ("sigma_adaptive", ctypes.c_int), ("sigma", ctypes.c_double),
         ("c3", ctypes.c_double), ("c4", ctypes.c_double),
+        ("sample_all", ctypes.c_int), ("sample_threshold", ctypes.c_ulonglong),
+        ("sample_seed", ctypes.c_ulonglong),
     ]
 
 
@@ -223,6 +225,8 @@ def _lib():
         lib.fc4o_occupation_factor.restype = ctypes.c_double
         lib.fc4o_sigma.argtypes = [P, ctypes.c_int, ctypes.c_int]
         lib.fc4o_sigma.restype = ctypes.c_double
+        lib.fc4o_splitmix64_mix.argtypes = [ctypes.c_ulonglong]
+        lib.fc4o_splitmix64_mix.restype = ctypes.c_ulonglong
         _LIB = lib
     return _LIB
 
@@ -244,6 +248,21 @@ def _ptr(a: np.ndarray):
 SIGMA_THZ_TO_RADPS = 2.0 * math.pi
 
 
+def sample_threshold(fraction: float) -> tuple[int, int]:
+    """(take every pair, threshold) of the four-phonon sampling estimate: a partner pair is taken
+    iff its 64-bit hash is below floor(f 2^64); f >= 1 takes every pair."""
+    if not (fraction > 0.0):
+        raise ValueError("the sampling fraction must be > 0")
+    if fraction >= 1.0:
+        return 1, 0xFFFFFFFFFFFFFFFF
+    return 0, int(math.ldexp(fraction, 64))
+
+
+def splitmix64_mix(z: int) -> int:
+    """The oracle's SplitMix64 output function (C), for its pins."""
+    return int(_lib().fc4o_splitmix64_mix(z & 0xFFFFFFFFFFFFFFFF))
+
+
 class Problem:
     """A crystal, its clusters, a mesh, the harmonic modes and (T, σ): the oracle's input.
 
@@ -252,7 +271,8 @@ class Problem:
     with ``sigma_adaptive``, the scale factor of the adaptive width."""
 
     def __init__(self, crystal, phi2, phi3, phi4, mesh, T=300.0, sigma=0.1,
-                 sigma_adaptive=False, modes: Modes | None = None):
+                 sigma_adaptive=False, modes: Modes | None = None, sample_fraction: float = 1.0,
+                 sample_seed: int = 0):
         self.crystal, self.phi2, self.phi3, self.phi4 = crystal, phi2, phi3, phi4
         self.mesh = tuple(int(x) for x in mesh)
         self.nq = int(np.prod(self.mesh))
@@ -261,6 +281,8 @@ class Problem:
         self.sigma = float(sigma)
         self.sigma_adaptive = bool(sigma_adaptive)
         self.modes = modes if modes is not None else harmonic(crystal, phi2, self.mesh)
+        self.sample_fraction = float(sample_fraction)
+        self.sample_seed = int(sample_seed)
         self._refresh()
 
     def _refresh(self):
@@ -293,16 +315,24 @@ class Problem:
         s.sigma_adaptive = int(self.sigma_adaptive)
         s.sigma = self.sigma * (1.0 if self.sigma_adaptive else SIGMA_THZ_TO_RADPS)
         s.c3, s.c4 = C3, C4
+        s.sample_all, s.sample_threshold = sample_threshold(self.sample_fraction)
+        s.sample_seed = self.sample_seed & 0xFFFFFFFFFFFFFFFF
         self._s = s
 
     def with_anharmonic(self, phi3=None, phi4=None) -> "Problem":
         """Same problem and modes with replaced Φ3 / Φ4 clusters."""
         return Problem(self.crystal, self.phi2, phi3 or self.phi3, phi4 or self.phi4, self.mesh,
-                       self.T, self.sigma, self.sigma_adaptive, self.modes)
+                       self.T, self.sigma, self.sigma_adaptive, self.modes, self.sample_fraction,
+                       self.sample_seed)
 
     def with_T(self, T: float) -> "Problem":
         return Problem(self.crystal, self.phi2, self.phi3, self.phi4, self.mesh, T, self.sigma,
-                       self.sigma_adaptive, self.modes)
+                       self.sigma_adaptive, self.modes, self.sample_fraction, self.sample_seed)
+
+    def with_sampling(self, fraction: float, seed: int) -> "Problem":
+        """Same problem with the four-phonon sampling estimate (fraction f of partner pairs)."""
+        return Problem(self.crystal, self.phi2, self.phi3, self.phi4, self.mesh, self.T, self.sigma,
+                       self.sigma_adaptive, self.modes, fraction, seed)
 
     # -- calls into the C oracle -----------------------------------------------------------
     def rates(self, modes=None, channel_mask: int = 31, qp_limit: int = 0):

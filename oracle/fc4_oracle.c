@@ -38,6 +38,17 @@
  * velocities equal by symmetry give a σ of rounding noise (~1e-15) whose 1/σ weight is meaningless.
  * Acoustic modes at Γ (q index 0, branches 0..2) are excluded as the mode and as partners.
  * Units: ω rad/ps, e dimensionless, Φ eV/Å^k, masses amu, Γ ps^-1 (C3, C4 come from Python).
+ *
+ * Sampling estimate (the paper's Results section names combining the GPU with sampling estimation
+ * as future work; it does not state the scheme, so this is a reading): for the four-phonon
+ * channels each partner pair (λ, q', q'') enters the sums independently with probability f, decided
+ * by a counter-based hash, and the sums of Γ and WP are multiplied by 2^64 / threshold (1/f up to
+ * the rounding of the threshold), an unbiased Monte-Carlo estimate of the full sums.  The hash is
+ * SplitMix64's output function (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) applied to seed + (key + 1) * 0x9e3779b97f4a7c15 with
+ * key = (mode * nq + q') * nq + q''; the pair is taken iff the hash is below threshold =
+ * floor(f 2^64) (threshold = 2^64 - 1 with every pair taken when f = 1).  Counts report the
+ * processes of the sampled pairs (not rescaled).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,6 +76,8 @@ typedef struct {
     int sigma_adaptive;       /* 0: fixed σ, 1: adaptive */
     double sigma;             /* fixed: σ in rad/ps; adaptive: scale factor */
     double c3, c4;            /* unit constants of Γ3, Γ4 (ps^-1 per unit sum) */
+    int sample_all;           /* 1: every four-phonon partner pair (no sampling) */
+    unsigned long long sample_threshold, sample_seed;   /* sampling estimate (see above) */
 } fc4o_problem;
 
 typedef struct { double re, im; } cplx;
@@ -121,6 +134,21 @@ static double q_dot_R(const fc4o_problem *p, const double q[3], const int n[3]) 
 }
 
 static int excluded(int iq, int j) { return iq == 0 && j < 3; }
+
+/* SplitMix64's output function (the mixing of the state into one 64-bit output) */
+unsigned long long fc4o_splitmix64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* 1 iff the four-phonon partner pair (mode m0, q1, q2) belongs to the sample */
+static int pair_sampled(const fc4o_problem *p, int m0, int q1, int q2) {
+    if (p->sample_all) return 1;
+    unsigned long long key = ((unsigned long long)m0 * p->nq + q1) * p->nq + q2;
+    unsigned long long z = p->sample_seed + (key + 1ull) * 0x9e3779b97f4a7c15ull;
+    return fc4o_splitmix64_mix(z) < p->sample_threshold;
+}
 
 /* eigenvector component (3*atom + cart) of branch j at q, conjugated when conj != 0 */
 static cplx evec(const fc4o_problem *p, int iq, int comp, int j, int conj) {
@@ -319,6 +347,7 @@ static void enumerate(const fc4o_problem *p, int ch, int m0, int qp_limit, visit
                 if (excluded(q1, j1)) continue;
                 int m1 = q1 * nb + j1;
                 for (int q2 = 0; q2 < N; q2++) {
+                    if (!pair_sampled(p, m0, q1, q2)) continue;
                     int q3 = q_combine(p, 1, q0, s1, q1, s2, q2);
                     for (int j2 = 0; j2 < nb; j2++) {
                         if (excluded(q2, j2)) continue;
@@ -381,8 +410,10 @@ int fc4o_rates(const fc4o_problem *p, int n_modes, const int *modes, int channel
             if (channel_mask & (1 << ch)) enumerate(p, ch, modes[i], qp_limit, rate_visit, &a);
             double norm = (ch < 2) ? N : N * N;
             double cst = (ch < 2) ? p->c3 : p->c4;
-            gamma[(size_t)ch * n_modes + i] = a.gamma * cst / norm;
-            wp[(size_t)ch * n_modes + i] = a.wp / norm;
+            /* sampled four-phonon sums scaled by the inverse inclusion probability 2^64 / threshold */
+            double scale = (ch < 2 || p->sample_all) ? 1.0 : ldexp(1.0, 64) / (double)p->sample_threshold;
+            gamma[(size_t)ch * n_modes + i] = a.gamma * scale * cst / norm;
+            wp[(size_t)ch * n_modes + i] = a.wp * scale / norm;
             counts[(size_t)ch * n_modes + i] = a.count;
         }
     }

@@ -138,24 +138,32 @@ fc4_status fc4_rates(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_
                      int channel_mask, const int *q_subset, int n_q, double *gamma_out,
                      double *wp_out, long long *counts_out, void *stream);
 
-/* fc4_rates_static - fc4_rates for callers that must not allocate device memory during the call.
- * The paper has no counterpart: this entry point exists for integrations where device allocation
- * is not allowed at the point of the call, e.g. code running inside CUDA stream capture (a
- * cudaMalloc there breaks the capture), or host frameworks that own every device allocation
- * through their own pool and forbid direct cudaMalloc/cudaFree from libraries.  Such callers
- * create the context once with fc4_init (which does allocate) during set-up, then use this call.
+/* fc4_rates_static - fc4_rates for callers that cannot allocate device memory during the call.
+ * The paper has no counterpart.  Some host programs own every byte of device memory through
+ * their own pooled allocator and do not let a library call cudaMalloc or cudaFree (a direct
+ * allocation escapes the pool's accounting, and cudaFree synchronises the whole device); others
+ * run latency-bound loops in which an allocation, with its implicit synchronisation, is not
+ * acceptable.  Such callers create the context once with fc4_init (which does allocate) during
+ * set-up, then call this entry point, which allocates nothing.
  *
- * Same kernels, arithmetic and results as fc4_rates (fixed σ only, q_subset required, no stats).
+ * Fixed σ only, q_subset required, no work counters (fc4_stats).  The three-phonon channels run
+ * the same kernels as fc4_rates.  The four-phonon channels run the general kernel, which builds
+ * W per block in shared memory, not the tiled path that fc4_rates takes for cells of up to two
+ * atoms (that path needs the large W buffer) and never the tensor-core contraction; kept counts
+ * are identical, Γ and WP agree with fc4_rates to rounding in FP64 and to the mixed tolerance
+ * (1e-4 relative) in mixed precision.
  * Its per-call scratch (q list, mode list, per-(channel, mode, q') partials) is one file-scope
  * device array of 13 MB, created when the library is loaded and held by every GPU that loads it
  * until the process exits.  Limit: n_q * nb * N <= 65536 (e.g. all 27 q of a 3x3x3 mesh, or up
  * to 21 q of an 8x8x8 two-atom mesh); larger requests return FC4_ERR_INVALID and write nothing.
  * No cudaMalloc, cudaFree or other allocating routine is called.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and caches it: make that first
- * call before any stream capture.  Every call reuses the same array, so calls that overlap on
- * the GPU (different streams, different contexts, different threads) race and give wrong
- * results; serialise them.  Nothing in the array is read before the same call has written it.
- * Does not change the state that fc4_rates_backward and fc4_processes read. */
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it, so make that first
+ * call before any stream capture.  q_subset (host) is copied into the array on the given stream
+ * at every call; if it is page-locked memory, keep it unchanged until the stream has passed the
+ * call.  Every call reuses the same array, so calls that overlap on the GPU (different streams,
+ * different contexts, different threads) race and give wrong results; serialise them.  Nothing
+ * in the array is read before the same call has written it.  Does not change the state that
+ * fc4_rates_backward and fc4_processes read. */
 fc4_status fc4_rates_static(fc4_ctx *ctx, double T_K, double sigma_value, int channel_mask,
                             const int *q_subset, int n_q, double *gamma_out, double *wp_out,
                             long long *counts_out, void *stream);

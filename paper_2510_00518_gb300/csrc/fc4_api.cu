@@ -1053,9 +1053,10 @@ void fc4_destroy(fc4_ctx *c) {
 
 // ------------------------------------------------------------------------------ allocation-free rates
 //
-// fc4_rates_static: the same kernels as fc4_rates, but every piece of per-call device scratch (the
-// q list, the mode list and the per-(channel, mode, q') partial sums) lives in one file-scope
-// __device__ array of fixed size, so the call itself allocates no device memory.  A host-side use
+// fc4_rates_static: fc4_rates without device allocation.  Every piece of per-call device scratch
+// (the q list, the mode list and the per-(channel, mode, q') partial sums) lives in one file-scope
+// __device__ array of fixed size.  With no W buffer to hand, the four-phonon channels take the
+// general kernel (W built per block in shared memory) instead of the tiled W-buffer path.  A host-side use
 // of the array's name is only a stand-in for it; the device address is looked up once per device
 // with cudaGetSymbolAddress and cached.
 
@@ -1139,18 +1140,11 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
     a.part_items = part_items;
     a.part_ent = part_ent;
     const int fp64 = c->precision == FC4_FP64;
-    const size_t chunk = (size_t)nm * N;
     for (int ch = 0; ch < 5; ++ch) {
         if (!((channel_mask >> ch) & 1)) continue;
-        const bool empty = ch < 2 ? c->nc3 == 0 : c->nc4 == 0;
-        if (empty) {                                   // the only partials read without a write
-            FC4_CUDA(c, cudaMemsetAsync(part_g + ch * chunk, 0, chunk * sizeof(double), s));
-            FC4_CUDA(c, cudaMemsetAsync(part_wp + ch * chunk, 0, chunk * sizeof(double), s));
-            FC4_CUDA(c, cudaMemsetAsync(part_n + ch * chunk, 0, chunk * sizeof(long long), s));
-            FC4_CUDA(c, cudaMemsetAsync(part_items + ch * chunk, 0, chunk * sizeof(long long), s));
-            FC4_CUDA(c, cudaMemsetAsync(part_ent + ch * chunk, 0, chunk * sizeof(long long), s));
-            continue;
-        }
+        // A channel without clusters launches nothing: its a.n_part[ch] stays 0, so the reduction
+        // reads no partials and writes Γ = WP = 0 and count 0 for it.
+        if (ch < 2 ? c->nc3 == 0 : c->nc4 == 0) continue;
         if (ch < 2) FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));
         else FC4_CUDA(c, fc4::launch_rates4(c->t, a, ch, fp64, c->block_threads, s));
     }

@@ -1,0 +1,67 @@
+"""Writes the oracle's expected values for the two large parity workloads, with the harmonic modes
+they were computed from (so that a test injects the same ω bits and eigenvector gauge):
+
+  config2_8cubed.npz   seed-0 Morse diamond, 8x8x8 mesh, fixed σ = 0.1 THz, the 8 q points
+                       numpy default_rng(0).choice(512, 8) (sorted) x 6 branches, T = 300 K and 700 K
+  config3_16cubed.npz  seed-1 Morse diamond, 16x16x16 mesh, adaptive σ (scale 1), T = 300 K, the
+                       first q point of default_rng(1).choice(4096, 145) (sorted) x 6 branches
+
+Each file holds q, omega [N nb], vel [N nb, 3], evec [N, nb, nb] (complex), T [nT] and, per T,
+gamma, wp [nT, 5, n_modes] and counts [nT, 5, n_modes] for the channels 3ph+, 3ph-, 4ph++,
+4ph+-, 4ph-- (Algorithms 1 and 4: Γ = C/N^k Σ WP |V|², WP, kept counts).  Only oracle/ and synth/
+are called.  Run from the repository root (OpenMP over modes; the 16^3 case takes hours of
+one core per mode):
+
+    python tests/golden/make_config_goldens.py config2
+    python tests/golden/make_config_goldens.py config3
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+CASES = {
+    "config2": dict(seed=0, n=8, k=8, sample_seed=0, take=8, sigma=0.1, adaptive=False,
+                    temps=(300.0, 700.0), out="config2_8cubed.npz"),
+    "config3": dict(seed=1, n=16, k=145, sample_seed=1, take=1, sigma=1.0, adaptive=True,
+                    temps=(300.0,), out="config3_16cubed.npz"),
+}
+
+
+def run(name):
+    import oracle
+    from synth import morse_system, sample_q
+    c = CASES[name]
+    sysm = morse_system(seed=c["seed"])
+    mesh = (c["n"],) * 3
+    N = c["n"] ** 3
+    q = sample_q(N, c["k"], c["sample_seed"])[:c["take"]]
+    nb = sysm[0].nb
+    modes = np.array([qq * nb + j for qq in q for j in range(nb)], np.int32)
+    base = oracle.Problem(*sysm, mesh, T=c["temps"][0], sigma=c["sigma"], sigma_adaptive=c["adaptive"])
+    gs, wps, cnts = [], [], []
+    for T in c["temps"]:
+        P = base.with_T(T)
+        t0 = time.time()
+        g, wp, cnt = P.rates(modes)
+        print(f"{name}: T = {T} K, {modes.size} modes, {cnt.sum()} kept, {time.time() - t0:.0f} s", flush=True)
+        gs.append(g)
+        wps.append(wp)
+        cnts.append(cnt)
+    m = base.modes
+    np.savez_compressed(os.path.join(HERE, c["out"]), q=q.astype(np.int32), modes=modes,
+                        mesh=np.array(mesh, np.int32), seed=np.int32(c["seed"]),
+                        sigma=np.float64(c["sigma"]), adaptive=np.int32(c["adaptive"]),
+                        T=np.array(c["temps"]), omega=m.omega, vel=m.vel, evec=m.evec,
+                        gamma=np.array(gs), wp=np.array(wps), counts=np.array(cnts))
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:] or ["config2"]:
+        run(name)

@@ -50,10 +50,26 @@ typedef enum {
 } fc4_status;
 
 /* Arithmetic of the matrix-element contraction.  The energy window, the process counts and the
- * final reduction into Γ are FP64 in every mode. */
+ * final reduction into Γ are FP64 in every mode (the window decided exactly, the sums
+ * accumulated per thread in Kahan FP32 or FP64 and across threads in FP64).
+ *   FC4_FP64    every channel: FP64 contraction and FP64 weights (reference-accurate)
+ *   FC4_MIXED   four-phonon channels: FP32 contraction and FP32 weights on the CUDA cores;
+ *               three-phonon channels: FP64 (their acoustic-sum-rule cancellations need it)
+ * The tensor-core modes are FC4_MIXED with the cluster contraction X = Σ_r P_r W_r of the 4ph +-
+ * channel (the dense one) run by tcgen05.mma with FP32 accumulation in tensor memory, for cells
+ * of two atoms (other cells, and the sparse ++ and -- channels, stay on the CUDA cores):
+ *   FC4_TF32X3  TF32 hi/lo operand splits, three products (hi.hi + hi.lo + lo.hi): ~2^-21 relative
+ *   FC4_BF16    BF16 operands, one product: ~2^-8 relative (single pass; Γ off by ~1e-3)
+ *   FC4_BF16X3  BF16 hi/lo splits, three products: ~2^-16 relative
+ *   FC4_FP16X3  FP16 hi/lo splits of W scaled by a power of two per unit, three products: ~2^-21
+ * Mixed-precision arithmetic is the paper's named direction for further speed (Results, end). */
 typedef enum {
-    FC4_FP64 = 0,          /* FP64 contraction and FP64 weights (reference-accurate) */
-    FC4_MIXED = 1          /* FP32 contraction and FP32 weights, FP64 window and accumulation */
+    FC4_FP64 = 0,
+    FC4_MIXED = 1,
+    FC4_TF32X3 = 2,
+    FC4_BF16 = 3,
+    FC4_BF16X3 = 4,
+    FC4_FP16X3 = 5
 } fc4_precision;
 
 typedef struct {
@@ -232,7 +248,26 @@ fc4_status fc4_timings(fc4_ctx *ctx, double out[9]);
  * than 2 atoms): 64, 96 or 128 (0 = 128).  A tuning knob; results do not depend on it. */
 fc4_status fc4_set_block_threads(fc4_ctx *ctx, int block_threads);
 
-/* fc4_set_tensor_cores - on = 1: in mixed precision, two-atom cells, the
+/* fc4_set_mode_chunk - how many modes one fc4_rates call processes at a time (the paper's
+ * all-modes and mode-by-mode strategies, Results and Algorithm 5).  A call splits its modes into
+ * chunks of at most modes_per_chunk modes (0: no bound) and of at most w_limit_bytes of W scratch
+ * for the tiled 4ph path (0: max(4 GiB, a quarter of the device memory)); each chunk runs every
+ * channel and its reduction before the next.  The per-call device memory (partials of 56 bytes
+ * per (channel, mode, q'), and W of fc4_memory's out[1] bytes per mode) grows with the chunk, not
+ * with the subset.  modes_per_chunk = 1 is mode by mode.  Results do not depend on the chunking. */
+fc4_status fc4_set_mode_chunk(fc4_ctx *ctx, int modes_per_chunk, long long w_limit_bytes);
+
+/* fc4_memory - device memory of a context: out[0] bytes allocated by the context in total,
+ * out[1] W bytes per mode of the tiled 4ph path in the current precision (0: general kernel),
+ * out[2] bytes of the current W buffer, out[3] bytes of the current partials, out[4] modes per
+ * chunk of the last fc4_rates call. */
+fc4_status fc4_memory(const fc4_ctx *ctx, long long out[5]);
+
+/* fc4_set_precision - change the arithmetic of later fc4_rates calls (any fc4_precision; the
+ * tables of every mode are built at fc4_init).  Kept sets do not depend on it. */
+fc4_status fc4_set_precision(fc4_ctx *ctx, int precision);
+
+/* fc4_set_tensor_cores - on = 1: in mixed precision (FC4_MIXED), two-atom cells, the
  * cluster contraction X = Σ_r P_r W_r of the 4ph +- channel runs on the tensor cores (tcgen05,
  * FP16 hi/lo operands, three products, FP32 accumulation: FP32-level accuracy).  on = 0 (the
  * default, faster on this workload): CUDA cores only.  Kept sets are identical either way; Γ agrees to rounding.  Other channels, the FP64

@@ -14,9 +14,14 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "CHANNELS", "lib_path", "rates_fn", "kappa_fn"]
+__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "TF32X3", "BF16", "BF16X3", "FP16X3",
+           "PRECISIONS", "CHANNELS", "lib_path", "rates_fn", "kappa_fn"]
 
-FP64, MIXED = 0, 1
+# fc4_precision: FP64; FP32 on the CUDA cores; and the tensor-core operand formats of the 4ph +-
+# contraction (two-atom cells)
+FP64, MIXED, TF32X3, BF16, BF16X3, FP16X3 = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "tf32x3": TF32X3, "bf16": BF16, "bf16x3": BF16X3,
+              "fp16x3": FP16X3}
 CHANNELS = ("3ph+", "3ph-", "4ph++", "4ph+-", "4ph--")
 STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "UNSTABLE", 6: "STATE"}
 
@@ -79,6 +84,9 @@ def load(build_if_missing: bool = False):
         "fc4_rates_static": [vp, d, d, i, vp, i, vp, vp, vp, vp],
         "fc4_set_block_threads": [vp, i],
         "fc4_set_tensor_cores": [vp, i],
+        "fc4_set_precision": [vp, i],
+        "fc4_set_mode_chunk": [vp, i, ll],
+        "fc4_memory": [vp, vp],
         "fc4_check_device": [vp],
         "fc4_symmetry_ops": [ctypes.POINTER(_Crystal), ctypes.POINTER(_IFC), ctypes.POINTER(_IFC),
                              ctypes.POINTER(_IFC), d, i, vp, vp, vp],
@@ -200,6 +208,23 @@ class Engine:
         self._check(self.lib.fc4_info(self.ctx, _ptr(out)))
         keys = ("n_atoms", "nb", "N", "nc2", "nc3", "nc4", "n_keys", "precision")
         return dict(zip(keys, out.tolist()))
+
+    def set_precision(self, precision: int):
+        """Arithmetic of later rates calls (FP64, MIXED, TF32X3, BF16, BF16X3, FP16X3)."""
+        self._check(self.lib.fc4_set_precision(self.ctx, int(precision)))
+        self.precision = int(precision)
+
+    def set_mode_chunk(self, modes_per_chunk: int = 0, w_limit_bytes: int = 0):
+        """Modes per chunk of a rates call (0: all modes at once, 1: mode by mode) and the cap of
+        the W scratch in bytes (0: the default cap)."""
+        self._check(self.lib.fc4_set_mode_chunk(self.ctx, int(modes_per_chunk), int(w_limit_bytes)))
+
+    def memory(self) -> dict:
+        """Device memory of the context (bytes) and the chunking of the last rates call."""
+        out = np.zeros(5, np.int64)
+        self._check(self.lib.fc4_memory(self.ctx, _ptr(out)))
+        return {"total": int(out[0]), "w_per_mode": int(out[1]), "w_buffer": int(out[2]),
+                "partials": int(out[3]), "modes_per_chunk": int(out[4])}
 
     def set_tensor_cores(self, on: bool):
         """Tensor-core cluster contraction of the 4ph +- channel (mixed precision, <= 2 atoms)."""

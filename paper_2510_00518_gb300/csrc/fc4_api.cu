@@ -57,6 +57,7 @@ struct fc4_ctx {
     long long n_launches = 0;
     double volume = 0.0;
     std::vector<void *> owned;
+    std::map<void *, size_t> alloc_bytes;  // size of each allocation (entries of freed ones are stale)
     std::vector<int> perm4;                 // device cluster slot -> input cluster index
     std::vector<int> swap12, swap23;        // input cluster -> the cluster with legs 1,2 (2,3) swapped
     bool sym12 = false, sym23 = false;      // Φ4 invariant under those swaps (triangular domains)
@@ -84,6 +85,9 @@ struct fc4_ctx {
     void *wbuf = nullptr;                  // W scratch of the tiled 4ph path
     size_t wbuf_bytes = 0;
     int w_s1 = 0;                          // sign s1 of the W held for w_modes (0: none)
+    int mode_chunk = 0;                    // modes per chunk of a rates call (0: as many as W allows)
+    size_t w_limit = 0;                    // cap of the W buffer in bytes (0: max(4 GiB, HBM / 4))
+    int last_chunk = 0;                    // modes per chunk of the last rates call
     std::vector<int> w_modes;
     int *perm4_dev = nullptr;              // device cluster slot -> input index (gradients)
     double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
@@ -123,7 +127,10 @@ cudaError_t dalloc(fc4_ctx *c, T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
     cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-    if (e == cudaSuccess) c->owned.push_back(*p);
+    if (e == cudaSuccess) {
+        c->owned.push_back(*p);
+        c->alloc_bytes[(void *)*p] = n * sizeof(T);
+    }
     return e;
 }
 
@@ -250,13 +257,26 @@ void prefilter(const fc4_ctx *c, double two_sigma, float *lo, float *hi) {
     *hi = std::nextafter((float)(two_sigma + 2.0 * eps), 1e30f);
 }
 
+// Operand format of the tensor-core +- contraction for a context (the launcher's a.use_tc):
+// 0 none (CUDA cores), 1 FP16 x3, 2 BF16 x3, 3 BF16, 4 TF32 x3.
+int tc_op(const fc4_ctx *c) {
+    switch (c->precision) {
+        case FC4_MIXED: return c->use_tc ? 1 : 0;
+        case FC4_FP16X3: return 1;
+        case FC4_BF16X3: return 2;
+        case FC4_BF16: return 3;
+        case FC4_TF32X3: return 4;
+        default: return 0;
+    }
+}
+
 // Window and Gaussian parameters of a rates call: fixed σ = 2π sigma_value rad/ps, or adaptive
 // σ = s |ΔP| / sqrt(6) with s = sigma_value.  For the adaptive prefilter, Q = max|v| max_k |b_k| / n_k
 // bounds every |P_k| and the FP64 rounding of the exact σ (<= 2^-50 Q per component); the margins
 // are those stated with the kernels' window test.
 void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_value) {
     a.adaptive = adaptive ? 1 : 0;
-    a.use_tc = (c->use_tc && c->precision == FC4_MIXED && fc4::tc_supported(c->t)) ? 1 : 0;
+    a.use_tc = fc4::tc_supported(c->t) ? tc_op(c) : 0;
     a.spin_limit = c->timeout_cycles;
     a.err = c->dev_err;
     a.n_kernels = const_cast<long long *>(&c->n_launches);
@@ -322,7 +342,7 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
 
     fc4_ctx *c = new fc4_ctx();
     if (opt) {
-        if (opt->precision != FC4_FP64 && opt->precision != FC4_MIXED) {
+        if (opt->precision < FC4_FP64 || opt->precision > FC4_FP16X3) {
             delete c;
             return fail(nullptr, FC4_ERR_INVALID, "unknown precision");
         }
@@ -698,7 +718,21 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         c->modes_cap = nm;
         c->modes_on_device.clear();
     }
-    const size_t need = (size_t)5 * nm * N;
+    // Modes are processed in chunks.  All modes in one chunk is the paper's all-modes strategy;
+    // fc4_set_mode_chunk bounds the chunk (1: mode by mode, Algorithm 5), and the W buffer of the
+    // tiled 4ph path caps it at max(4 GiB, a quarter of the device memory).  Partials and W are
+    // sized for one chunk, so the call's memory grows with the chunk, not with the subset.
+    const bool need_w = (channel_mask & 0b11100) && c->nc4;
+    const size_t per_mode = need_w ? fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64) : 0;
+    size_t chunk = (size_t)nm;
+    if (c->mode_chunk > 0) chunk = std::min(chunk, (size_t)c->mode_chunk);
+    if (per_mode) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+        const size_t cap_bytes = c->w_limit ? c->w_limit : std::max<size_t>(4ull << 30, total_b / 4);
+        chunk = std::max<size_t>(1, std::min(chunk, cap_bytes / per_mode));
+    }
+    const size_t need = (size_t)5 * chunk * N;
     if (need > c->part_cap) {
         for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items,
                         (void *)c->part_ent, (void *)c->part_ev, (void *)c->part_cev})
@@ -715,97 +749,75 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         FC4_CUDA(c, dalloc(c, &c->part_cev, need));
         c->part_cap = need;
     }
+    if (per_mode && c->wbuf_bytes < chunk * per_mode) {     // W scratch of the tiled 4ph path
+        if (c->wbuf) {
+            cudaFree(c->wbuf);
+            c->owned.erase(std::find(c->owned.begin(), c->owned.end(), c->wbuf));
+            c->wbuf = nullptr;
+            c->wbuf_bytes = 0;
+        }
+        unsigned char *w = nullptr;
+        FC4_CUDA(c, dalloc(c, &w, chunk * per_mode));
+        c->wbuf = w;
+        c->wbuf_bytes = chunk * per_mode;
+        c->w_s1 = 0;
+    }
     if (modes != c->modes_on_device) {      // unchanged subsets need no copy (stream capture)
         FC4_CUDA(c, cudaMemcpyAsync(c->modes, modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
         c->modes_on_device = modes;
     }
     fc4_status st = ensure_occupations(c, T_K, s);
     if (st != FC4_OK) return st;
-    fc4::RateArgs a{};
-    a.n_modes = nm;
-    a.modes = c->modes;
-    set_window(c, a, sigma_adaptive != 0, sigma_value);
-    a.part_g = c->part_g;
-    a.part_wp = c->part_wp;
-    a.part_n = c->part_n;
-    a.part_items = c->part_items;
-    a.part_ent = c->part_ent;
-    a.part_ev = c->part_ev;
-    a.part_cev = c->part_cev;
-    size_t w_per_mode = 0;
-    {   // W scratch of the tiled 4ph path, in whole modes, grown on demand: up to a quarter of the
-        // device memory (at least 4 GiB), so that typical mode sets fit in one chunk and the ++ and
-        // +- channels share one W
-        const size_t per_mode = fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64);
-        w_per_mode = per_mode;
-        if (per_mode && (channel_mask & 0b11100) && c->nc4) {
-            size_t free_b = 0, total_b = 0;
-            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
-            const size_t cap_bytes = std::max<size_t>(4ull << 30, total_b / 4);
-            const size_t cap_modes = std::max<size_t>(1, std::min<size_t>((size_t)nm, cap_bytes / per_mode));
-            const size_t want = cap_modes * per_mode;
-            if (c->wbuf_bytes < want) {
-                if (c->wbuf) {
-                    cudaFree(c->wbuf);
-                    c->owned.erase(std::find(c->owned.begin(), c->owned.end(), c->wbuf));
-                    c->wbuf = nullptr;
-                    c->wbuf_bytes = 0;
-                }
-                unsigned char *w = nullptr;
-                FC4_CUDA(c, dalloc(c, &w, want));
-                c->wbuf = w;
-                c->wbuf_bytes = want;
-                c->w_s1 = 0;
-            }
-        }
-        a.wbuf = c->wbuf;
-        a.wbuf_bytes = c->wbuf_bytes;
-    }
     if (!c->stats) FC4_CUDA(c, dalloc(c, &c->stats, 25));
     FC4_CUDA(c, cudaMemsetAsync(c->stats, 0, 25 * sizeof(unsigned long long), s));
     const int fp64 = c->precision == FC4_FP64;
-    for (int ch = 0; ch < 5; ++ch) {
-        if (!((channel_mask >> ch) & 1)) continue;
-        if (ch < 2) {
-            if (c->nc3 == 0) {
-                FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
-                for (long long *p : {c->part_items, c->part_ent, c->part_ev, c->part_cev})
-                    FC4_CUDA(c, cudaMemsetAsync(p + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
-                continue;
-            }
-            Timed tm(c, ch, s);
-            FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));
-        } else {
-            if (c->nc4 == 0) {
-                FC4_CUDA(c, cudaMemsetAsync(c->part_g + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_wp + (size_t)ch * nm * N, 0, sizeof(double) * nm * N, s));
-                FC4_CUDA(c, cudaMemsetAsync(c->part_n + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
-                for (long long *p : {c->part_items, c->part_ent, c->part_ev, c->part_cev})
-                    FC4_CUDA(c, cudaMemsetAsync(p + (size_t)ch * nm * N, 0, sizeof(long long) * nm * N, s));
+    c->last_chunk = (int)chunk;
+    for (size_t m0 = 0; m0 < (size_t)nm; m0 += chunk) {
+        const int cm = (int)std::min(chunk, (size_t)nm - m0);
+        fc4::RateArgs a{};
+        a.n_modes = cm;
+        a.modes = c->modes + m0;
+        set_window(c, a, sigma_adaptive != 0, sigma_value);
+        a.part_g = c->part_g;
+        a.part_wp = c->part_wp;
+        a.part_n = c->part_n;
+        a.part_items = c->part_items;
+        a.part_ent = c->part_ent;
+        a.part_ev = c->part_ev;
+        a.part_cev = c->part_cev;
+        a.wbuf = per_mode ? c->wbuf : nullptr;
+        a.wbuf_bytes = per_mode ? c->wbuf_bytes : 0;
+        const std::vector<int> cmodes(modes.begin() + m0, modes.begin() + m0 + cm);
+        for (int ch = 0; ch < 5; ++ch) {
+            if (!((channel_mask >> ch) & 1)) continue;
+            // a channel without clusters launches nothing: its a.n_part[ch] stays 0, so the
+            // reduction reads no partials and writes Γ = WP = 0 and count 0 for it
+            if (ch < 2 ? c->nc3 == 0 : c->nc4 == 0) continue;
+            if (ch < 2) {
+                Timed tm(c, ch, s);
+                FC4_CUDA(c, fc4::launch_rates3(c->t, a, ch, fp64, s));
                 continue;
             }
             const int s1 = ch == 4 ? -1 : 1;
-            const bool whole = w_per_mode && c->wbuf && (size_t)nm * w_per_mode <= c->wbuf_bytes;
-            a.w_reuse = whole && c->w_s1 == s1 && c->w_modes == modes;
+            const bool whole = per_mode && c->wbuf && (size_t)cm * per_mode <= c->wbuf_bytes;
+            a.w_reuse = whole && c->w_s1 == s1 && c->w_modes == cmodes;
             Timed tm(c, ch, s);
             FC4_CUDA(c, fc4::launch_rates4(c->t, a, ch, fp64, c->block_threads, s));
             if (whole && a.wbuf) {
                 c->w_s1 = s1;
-                if (c->w_modes != modes) c->w_modes = modes;
+                if (c->w_modes != cmodes) c->w_modes = cmodes;
             } else {
                 c->w_s1 = 0;
             }
         }
+        a.out_ld = nm;
+        Timed tm(c, 5, s);
+        FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out + m0,
+                                       wp_out ? wp_out + m0 : nullptr, counts_out ? counts_out + m0 : nullptr,
+                                       c->stats, s));
     }
     for (int k = 0; k < 5; ++k)
         if (!((channel_mask >> k) & 1)) c->ev_used[k] = false;
-    {
-        Timed tm(c, 5, s);
-        FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out, wp_out,
-                                       counts_out, c->stats, s));
-    }
     for (int ch = 0; ch < 5; ++ch) {
         const long long per = ch < 2 ? (long long)N * nb * nb : (long long)N * N * nb * nb * nb;
         c->cand[ch] = ((channel_mask >> ch) & 1) ? per * nm : 0;
@@ -1002,6 +1014,38 @@ fc4_status fc4_set_block_threads(fc4_ctx *c, int block_threads) {
     if (block_threads != 0 && block_threads != 64 && block_threads != 96 && block_threads != 128)
         return fail(c, FC4_ERR_INVALID, "block_threads must be 0, 64, 96 or 128");
     c->block_threads = block_threads ? block_threads : 128;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_mode_chunk(fc4_ctx *c, int modes_per_chunk, long long w_limit_bytes) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (modes_per_chunk < 0 || w_limit_bytes < 0)
+        return fail(c, FC4_ERR_INVALID, "modes_per_chunk and w_limit_bytes must be >= 0");
+    c->mode_chunk = modes_per_chunk;
+    c->w_limit = (size_t)w_limit_bytes;
+    return FC4_OK;
+}
+
+fc4_status fc4_memory(const fc4_ctx *c, long long out[5]) {
+    if (!c || !out) return FC4_ERR_INVALID;
+    long long tot = 0;
+    for (void *p : c->owned) {
+        auto it = c->alloc_bytes.find(p);
+        if (it != c->alloc_bytes.end()) tot += (long long)it->second;
+    }
+    out[0] = tot;
+    out[1] = (long long)fc4::rates4_wbuf_per_mode(c->t, c->precision == FC4_FP64);
+    out[2] = (long long)c->wbuf_bytes;
+    out[3] = (long long)c->part_cap * 7 * 8;
+    out[4] = c->last_chunk;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_precision(fc4_ctx *c, int precision) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (precision < FC4_FP64 || precision > FC4_FP16X3) return fail(c, FC4_ERR_INVALID, "unknown precision");
+    if (precision != c->precision) c->w_s1 = 0;     // the W buffer's element type may change
+    c->precision = precision;
     return FC4_OK;
 }
 

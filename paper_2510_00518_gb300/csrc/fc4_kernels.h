@@ -88,10 +88,12 @@ struct RateArgs {
     float ad_rlo, ad_rhi;        // prefilter: keep if |Δ32| <= ad_rlo 2σ32 - ad_e0,
     float ad_e0;                 //   reject if |Δ32| > ad_rhi 2σ32 + ad_e0, else exact FP64
     float ad_gmin;               // sure keep also needs 2σ32 > ad_gmin (σ above the noise floor)
-    int use_tc;                  // 1: tensor-core cluster contraction for 4ph +- (mixed, <= 2 atoms)
+    int use_tc;                  // tensor-core contraction of 4ph +- (two atoms): 0 off, 1 FP16 x3,
+                                 // 2 BF16 x3, 3 BF16, 4 TF32 x3
     long long spin_limit;        // bound (SM clocks) of device-side waits; 0 = default
     int *err;                    // device flag set by a kernel whose wait expired (may be NULL)
     long long *n_kernels;        // host counter of kernels launched (may be NULL; never read on device)
+    int out_ld;                  // row stride of the reduction's outputs [5][out_ld] (0: n_modes)
     int tri;                     // triangular 4ph domain allowed: bit 0 +- (Φ4 symmetric in legs 2, 3),
                                  // bit 1 ++ and -- (legs 1, 2; fixed σ only)
 };

@@ -263,7 +263,7 @@ struct int5 { int a, b, c, d, e; };
 
 // One warp per (channel, mode): lane l sums q' = l, l + 32, ... in order, then a fixed
 // butterfly; Γ = C / N^k * Σ, WP = Σ / N^k (k = 1 for 3ph, 2 for 4ph).
-__global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask, double c3, double c4,
+__global__ void reduce_kernel(int n_modes, int ld, int N, int5 n_part, int channel_mask, double c3, double c4,
                               const double *part_g, const double *part_wp, const long long *part_n,
                               const long long *part_items, const long long *part_ent, const long long *part_ev,
                               const long long *part_cev, double *gamma, double *wp, long long *counts,
@@ -309,9 +309,9 @@ __global__ void reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask,
         const double cst = ch < 2 ? c3 : c4;
         // a rate kernel whose bounded wait expired leaves incomplete partials: poison Γ
         if (err && *err) g = __longlong_as_double(0x7ff8000000000000ll);
-        gamma[(size_t)ch * n_modes + ms] = g * cst / norm;
-        if (wp) wp[(size_t)ch * n_modes + ms] = p / norm;
-        if (counts) counts[(size_t)ch * n_modes + ms] = n;
+        gamma[(size_t)ch * ld + ms] = g * cst / norm;
+        if (wp) wp[(size_t)ch * ld + ms] = p / norm;
+        if (counts) counts[(size_t)ch * ld + ms] = n;
     }
 }
 
@@ -323,7 +323,7 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
     int5 np;
     np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
     reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
+        a.n_modes, a.out_ld > 0 ? a.out_ld : a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
         a.part_ev, a.part_cev, gamma, wp, counts, stats, a.err);
     return cudaGetLastError();
 }

@@ -7,11 +7,14 @@
 // every (c, d) key group is one real matrix product covering all partner branches j':
 //   [Xr | Xi](q'', j' γδ) = [Pr | s2 Pi](q'', r) . [[Wr, Wi], [-Wi, Wr]](r, j' γδ)
 // (rows q'' = MMA M = 128 = TMEM lanes; K = 2 x keys of the group, padded to 16; N = 112 columns
-// of which 108 hold the 6 x 9 complex (j', γδ)).  Operands are FP16 hi/lo splits (W scaled by a
-// power of two per unit so that max |W| < 1); the three products hi.hi + hi.lo + lo.hi accumulate
-// in FP32 in tensor memory: relative accuracy ~2^-21, the level of the FP32 CUDA-core
-// contraction.  B is built once per unit, A once per round; one thread issues tcgen05.mma
-// (kind::f16) and tcgen05.commit to an mbarrier.  The three warpgroups then share the 128 rows:
+// of which 108 hold the 6 x 9 complex (j', γδ)).  The FP32 operands enter the tensor cores in one
+// of four formats (W scaled by a power of two per unit so that max |W| < 1):
+//   FP16 x3   kind::f16, FP16 hi/lo splits, products hi.hi + hi.lo + lo.hi: ~2^-21 relative
+//   BF16 x3   kind::f16 with BF16 operands, hi/lo splits, three products: ~2^-16
+//   BF16      kind::f16 with BF16 operands, one product: ~2^-8 (single pass)
+//   TF32 x3   kind::tf32, TF32 hi/lo splits (round to nearest), three products: ~2^-21
+// all accumulating in FP32 in tensor memory.  B is built once per unit, A once per round; one
+// thread issues tcgen05.mma and tcgen05.commit to an mbarrier.  The three warpgroups then share the 128 rows:
 // warpgroup g reads X of partner branches j' = g and g + 3 for its row with tcgen05.ld and
 // evaluates that (q'', j') entry directly (Y = X e*''' per j''', V = e''.Y per kept j'', weights:
 // 2 for a swapped pair, 1 on the diagonal q'' = q''' with j'' = j''').
@@ -22,6 +25,7 @@
 // its tensor memory and returns.
 #include "k_rates4.cuh"
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -45,13 +49,59 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor of kind::f16: D FP32, A and B FP16, both K-major, M = 128, N = kTcN
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+// Operand formats of the contraction (fc4_precision of the context).
+enum TcOp { kOpF16x3 = 0, kOpBF16x3 = 1, kOpBF16 = 2, kOpTF32x3 = 3 };
 
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+template <int OP>
+struct TcFmt {
+    static constexpr int ES = OP == kOpTF32x3 ? 4 : 2;       // bytes per element
+    static constexpr int EPC = 16 / ES;                      // elements per 16-byte core-matrix row
+    static constexpr int KI = 32 / ES;                       // K of one MMA instruction
+    static constexpr int NPROD = OP == kOpBF16 ? 1 : 3;      // hi.hi (+ hi.lo + lo.hi)
+    static constexpr int NT = NPROD > 1 ? 2 : 1;             // operand tiles: hi (and lo)
+    // instruction descriptor: D FP32 (bit 4), A and B format (bits 7-9, 10-12: 0 FP16, 1 BF16,
+    // 2 TF32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    static constexpr uint32_t FMT = OP == kOpF16x3 ? 0u : OP == kOpTF32x3 ? 2u : 1u;
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) |
+                                      ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+};
+
+template <int OP>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    if constexpr (OP == kOpTF32x3)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(TcFmt<OP>::IDESC), "r"(acc) : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(TcFmt<OP>::IDESC), "r"(acc) : "memory");
+}
+
+// FP32 x -> operand bits hi (and lo = the rounding of x - hi), each in the low ES bytes
+template <int OP>
+__device__ __forceinline__ void split_op(float x, uint32_t &hi, uint32_t &lo) {
+    if constexpr (OP == kOpF16x3) {
+        const __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    } else if constexpr (OP == kOpTF32x3) {
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - __uint_as_float(h)));
+        hi = h;
+        lo = l;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = OP == kOpBF16 ? 0u : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    }
+}
+
+template <int ES>
+__device__ __forceinline__ void store_op(unsigned char *p, uint32_t v) {
+    if constexpr (ES == 4) *reinterpret_cast<uint32_t *>(p) = v;
+    else *reinterpret_cast<unsigned short *>(p) = (unsigned short)v;
 }
 
 // bounded wait for the completion of phase `phase` of an mbarrier, at most max_cycles SM clocks.
@@ -87,32 +137,31 @@ __device__ __forceinline__ void tmem_ld18(uint32_t addr, float (&v)[18]) {
     for (int k = 0; k < 18; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-__device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo) {
-    hi = __float2half_rn(x);
-    lo = __float2half_rn(x - __half2float(hi));
-}
-
-// byte offset of element (row, k) in a K-major no-swizzle FP16 tile with `rows` rows
+// byte offset of element (row, k) in a K-major no-swizzle tile with `rows` rows of ES-byte elements
+template <int ES>
 __device__ __forceinline__ uint32_t tile_off(int row, int k, int rows) {
-    return 128u * (uint32_t)((k >> 3) * (rows >> 3) + (row >> 3)) + 16u * (uint32_t)(row & 7) + 2u * (uint32_t)(k & 7);
+    constexpr int EPC = 16 / ES;
+    return 128u * (uint32_t)((k / EPC) * (rows >> 3) + (row >> 3)) + 16u * (uint32_t)(row & 7) +
+           (uint32_t)ES * (uint32_t)(k % EPC);
 }
 
 }  // namespace
 
 // Key layout of the contraction: group g = c NA + d holds keys [grp_start[g], grp_start[g+1]);
-// its K extent is 2 x keys padded to 16 halves, at offset koff[g] (halves) of the K axis.
+// its K extent is 2 x keys padded to the K of one MMA instruction (ki elements), at offset
+// koff[g] (elements) of the K axis.
 struct TcPlan {
-    int kt;                   // total K (halves)
+    int kt;                   // total K (elements)
     int koff[4], kpad[4], nkey[4], r0[4];
 };
 
-__host__ __device__ inline TcPlan tc_plan(const Tables &t) {
+__host__ __device__ inline TcPlan tc_plan(const Tables &t, int ki) {
     TcPlan p{};
     int o = 0;
     for (int g = 0; g < 4; ++g) {
         p.r0[g] = t.grp_start[g];
         p.nkey[g] = t.grp_start[g + 1] - t.grp_start[g];
-        p.kpad[g] = (2 * p.nkey[g] + 15) / 16 * 16;
+        p.kpad[g] = (2 * p.nkey[g] + ki - 1) / ki * ki;
         p.koff[g] = o;
         o += p.kpad[g];
     }
@@ -120,27 +169,32 @@ __host__ __device__ inline TcPlan tc_plan(const Tables &t) {
     return p;
 }
 
-// shared memory: A hi | A lo (128 x kt halves each) | B hi | B lo (112 x kt halves each)
-__host__ __device__ inline size_t tc_smem_bytes(const Tables &t) {
-    const TcPlan p = tc_plan(t);
-    return (size_t)2 * kTcRows * p.kt * 2 + (size_t)2 * kTcN * p.kt * 2 + 128;
+// shared memory: A hi [| A lo] (128 x kt elements each) | B hi [| B lo] (112 x kt elements each)
+template <int OP>
+inline size_t tc_smem_bytes(const Tables &t) {
+    using F = TcFmt<OP>;
+    const TcPlan p = tc_plan(t, F::KI);
+    return (size_t)F::NT * kTcRows * p.kt * F::ES + (size_t)F::NT * kTcN * p.kt * F::ES + 128;
 }
 
-template <bool ADA>
+template <bool ADA, int OP>
 __global__ void __launch_bounds__(kTcThreads, 1)
 rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch, int mode0,
                  int n_units, const float2 *__restrict__ wall) {
     constexpr int NA = 2, NB = 6, NG = 4;
+    using F = TcFmt<OP>;
+    constexpr int ES = F::ES;
     const int s1 = (ch == 4) ? -1 : 1;
     const int s2 = (ch == 2) ? 1 : -1;
     const int N = t.N, nk = t.n_keys;
-    const TcPlan pl = tc_plan(t);
+    const TcPlan pl = tc_plan(t, F::KI);
+    const uint32_t a_tile = (uint32_t)(kTcRows * ES) * pl.kt, b_tile = (uint32_t)(kTcN * ES) * pl.kt;
 
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    unsigned char *sA = tc_smem;                                         // hi, then lo at + 256 kt
-    unsigned char *sB = sA + (size_t)2 * kTcRows * pl.kt * 2;            // hi, then lo at + 224 kt
-    const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + 256u * pl.kt;
-    const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + 224u * pl.kt;
+    unsigned char *sA = tc_smem;                                         // hi, then lo at + a_tile
+    unsigned char *sB = sA + (size_t)F::NT * a_tile;                     // hi, then lo at + b_tile
+    const uint32_t a_hi = smem_u32(sA), a_lo = a_hi + a_tile;
+    const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + b_tile;
     __shared__ __align__(8) unsigned long long s_mbar;
     __shared__ uint32_t s_tmem;
     __shared__ double s_red[2 * 32];
@@ -169,7 +223,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // B padding (rows 108..111, K columns beyond 2 x keys) stays zero for the whole kernel
-    for (int k = tid; k < 2 * kTcN * pl.kt / 2; k += kTcThreads) reinterpret_cast<uint32_t *>(sB)[k] = 0u;
+    for (int k = tid; k < (int)(F::NT * b_tile / 4); k += kTcThreads) reinterpret_cast<uint32_t *>(sB)[k] = 0u;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -219,11 +273,11 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                 for (int u = 0; u < 4; ++u) {
                     const int n = 18 * j1 + 2 * gd + (u >> 1);
                     const int kk = pl.koff[g] + kr + ((u & 1) ? pl.nkey[g] : 0);
-                    __half h, l;
-                    split_f16(val[u], h, l);
-                    const uint32_t off = tile_off(n, kk, kTcN);
-                    *reinterpret_cast<__half *>(sB + off) = h;
-                    *reinterpret_cast<__half *>(sB + 224u * pl.kt + off) = l;
+                    uint32_t h, l;
+                    split_op<OP>(val[u], h, l);
+                    const uint32_t off = tile_off<ES>(n, kk, kTcN);
+                    store_op<ES>(sB + off, h);
+                    if constexpr (F::NT > 1) store_op<ES>(sB + b_tile + off, l);
                 }
             }
 
@@ -265,24 +319,30 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                 // A: row `row`, the warpgroup's groups (0 | 1, 2 | 3: its share of the row), FP16 hi / lo
                 const float2 *Prow = t.P4_32 + (size_t)(valid ? q2 : 0) * nk;
                 for (int g = (wg == 0 ? 0 : wg == 1 ? 1 : 3); g <= (wg == 0 ? 0 : wg == 1 ? 2 : 3); ++g) {
-                    for (int k = 0; k < pl.kpad[g]; k += 2) {
-                        float v[2];
+                    // one 16-byte core-matrix row (F::EPC consecutive K elements) per store: the 32
+                    // rows of a warp write 512 contiguous bytes, free of bank conflicts
+                    for (int k = 0; k < pl.kpad[g]; k += F::EPC) {
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                        for (int u = 0; u < 2; ++u) {
+                        for (int w = 0; w < 4; ++w) { hw[w] = 0u; lw[w] = 0u; }
+#pragma unroll
+                        for (int u = 0; u < F::EPC; ++u) {
                             const int kk = k + u;
                             float x = 0.0f;
                             if (valid && kk < 2 * pl.nkey[g]) {
                                 const float2 p = Prow[pl.r0[g] + (kk < pl.nkey[g] ? kk : kk - pl.nkey[g])];
                                 x = kk < pl.nkey[g] ? p.x : (float)s2 * p.y;
                             }
-                            v[u] = x;
+                            uint32_t h, l;
+                            split_op<OP>(x, h, l);
+                            const int sh = (u * ES * 8) & 31, wi = (u * ES) >> 2;
+                            hw[wi] |= h << sh;
+                            lw[wi] |= l << sh;
                         }
-                        __half h0, l0, h1, l1;
-                        split_f16(v[0], h0, l0);
-                        split_f16(v[1], h1, l1);
-                        const uint32_t off = tile_off(row, pl.koff[g] + k, kTcRows);
-                        *reinterpret_cast<__half2 *>(sA + off) = __halves2half2(h0, h1);
-                        *reinterpret_cast<__half2 *>(sA + 256u * pl.kt + off) = __halves2half2(l0, l1);
+                        const uint32_t off = tile_off<ES>(row, pl.koff[g] + k, kTcRows);
+                        *reinterpret_cast<uint4 *>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        if constexpr (F::NT > 1)
+                            *reinterpret_cast<uint4 *>(sA + a_tile + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
                 }
                 // window of this row for the warpgroup's partner branches: bit NB j3 + j2 set iff kept
@@ -310,19 +370,44 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                         }
                     if (tri < 0) okm = 0;                                // the swap of another row
                     else acc_cev += (long long)nj * NB * NB;
+                    if constexpr (ADA) {
+                        // the width of a pair (λ'', λ''') is formed once for both partner branches
+#pragma unroll 1
+                        for (int j3 = 0; j3 < NB; ++j3) {
+                            if (!((v3 >> j3) & 1u)) continue;
+                            const int m3 = q3 * NB + j3;
+                            const float4 h3 = t.vp32[m3], l3 = t.vp32lo[m3];
+                            float g32[NB];
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2)
+                                g32[j2] = a.ad_c32 * vel_diff_norm32(t.vp32[q2 * NB + j2], t.vp32lo[q2 * NB + j2], h3, l3);
+#pragma unroll
+                            for (int jj = 0; jj < nj; ++jj) {
+                                const int j1 = wg + 3 * jj;
+                                if (!((vm1 >> j1) & 1u)) continue;
+                                const float b = w0f + (float)s1 * t.om32[q1 * NB + j1];
+                                unsigned row = 0;
+#pragma unroll
+                                for (int j2 = 0; j2 < NB; ++j2) {
+                                    if (!((v2 >> j2) & 1u)) continue;
+                                    const float ad = fabsf((b + w2f[j2]) - w3f[j3]);
+                                    const int w = window_adaptive32(a, ad, g32[j2]);
+                                    if (w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2,
+                                                                                     m3, q2 * NB + j2, m3)))
+                                        row |= 1u << j2;
+                                }
+                                keep[jj] |= (unsigned long long)row << (NB * j3);
+                            }
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < nj; ++jj) keep[jj] &= okm;
+                    }
 #pragma unroll
                     for (int jj = 0; jj < nj; ++jj) {
                         const int j1 = wg + 3 * jj;
                         if (!((vm1 >> j1) & 1u)) continue;
                         const float b = w0f + (float)s1 * t.om32[q1 * NB + j1];
                         if constexpr (ADA) {
-                            unsigned long long kept = 0;
-                            for (int j3 = 0; j3 < NB; ++j3)
-                                if ((v3 >> j3) & 1u)
-                                    kept |= (unsigned long long)window_adaptive4_row<NB>(
-                                                t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
-                                            << (NB * j3);
-                            keep[jj] = kept & okm;
                         } else {
                             float t2[NB];
 #pragma unroll
@@ -357,12 +442,12 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                     asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
-                        for (int pz = 0; pz < 3; ++pz) {         // hi.hi, hi.lo, lo.hi
-                            const uint32_t ab = (pz == 2 ? a_lo : a_hi) + 256u * pl.koff[g];
-                            const uint32_t bb = (pz == 1 ? b_lo : b_hi) + 224u * pl.koff[g];
-                            for (int s = 0; s < pl.kpad[g] / 16; ++s)
-                                mma_f16(tmem + (uint32_t)(kTcN * g), smem_desc(ab + 4096u * s, 2048u, 128u),
-                                        smem_desc(bb + 3584u * s, 1792u, 128u), (pz > 0 || s > 0) ? 1u : 0u);
+                        for (int pz = 0; pz < F::NPROD; ++pz) {  // hi.hi (, hi.lo, lo.hi)
+                            const uint32_t ab = (pz == 2 ? a_lo : a_hi) + (uint32_t)(kTcRows * ES) * pl.koff[g];
+                            const uint32_t bb = (pz == 1 ? b_lo : b_hi) + (uint32_t)(kTcN * ES) * pl.koff[g];
+                            for (int s = 0; s < pl.kpad[g] / F::KI; ++s)
+                                mma_issue<OP>(tmem + (uint32_t)(kTcN * g), smem_desc(ab + 4096u * s, 2048u, 128u),
+                                              smem_desc(bb + 3584u * s, 1792u, 128u), (pz > 0 || s > 0) ? 1u : 0u);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -502,11 +587,11 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcCols));
 }
 
-template <bool ADA>
+template <bool ADA, int OP>
 static cudaError_t launch_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
                              cudaStream_t s) {
-    const size_t smem = tc_smem_bytes(t);
-    cudaError_t e = cudaFuncSetAttribute(rates4_tc_kernel<ADA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = tc_smem_bytes<OP>(t);
+    cudaError_t e = cudaFuncSetAttribute(rates4_tc_kernel<ADA, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -517,20 +602,32 @@ static cudaError_t launch_tc(const Tables &t, const RateArgs &a, int ch, int mod
     if (units > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::min<long long>(units, (long long)std::max(sms, 1));   // one CTA per SM
     if (grid == 0) return cudaSuccess;
-    rates4_tc_kernel<ADA><<<grid, kTcThreads, smem, s>>>(t, a, ch, mode0, (int)units, w);
+    rates4_tc_kernel<ADA, OP><<<grid, kTcThreads, smem, s>>>(t, a, ch, mode0, (int)units, w);
     return cudaGetLastError();
 }
 
-// Used for two-atom cells whose operands fit in shared memory (other cells keep the CUDA-core
-// kernels).
+template <int OP>
+static cudaError_t launch_tc_op(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
+                                cudaStream_t s) {
+    return a.adaptive ? launch_tc<true, OP>(t, a, ch, mode0, nm, w, s) : launch_tc<false, OP>(t, a, ch, mode0, nm, w, s);
+}
+
+// Used for two-atom cells whose operands fit in shared memory in every format (other cells keep
+// the CUDA-core kernels).
 bool tc_supported(const Tables &t) {
-    return t.n_atoms == 2 && tc_smem_bytes(t) <= 200 * 1024;
+    return t.n_atoms == 2 && tc_smem_bytes<kOpTF32x3>(t) <= 200 * 1024 && tc_smem_bytes<kOpF16x3>(t) <= 200 * 1024;
 }
 
 cudaError_t launch_rates4_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
                              cudaStream_t s) {
     if (t.n_atoms != 2) return cudaErrorInvalidValue;
-    return a.adaptive ? launch_tc<true>(t, a, ch, mode0, nm, w, s) : launch_tc<false>(t, a, ch, mode0, nm, w, s);
+    switch (a.use_tc) {
+        case 1: return launch_tc_op<kOpF16x3>(t, a, ch, mode0, nm, w, s);
+        case 2: return launch_tc_op<kOpBF16x3>(t, a, ch, mode0, nm, w, s);
+        case 3: return launch_tc_op<kOpBF16>(t, a, ch, mode0, nm, w, s);
+        case 4: return launch_tc_op<kOpTF32x3>(t, a, ch, mode0, nm, w, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace fc4

@@ -217,6 +217,38 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         if (tri == 2) row &= (2u << j3) - 1u;    // j'' <= j'''
                         okm |= (unsigned long long)row << (NB * j3);
                     }
+                // Adaptive σ: the width of a pair (λ'', λ''') does not depend on j', so each of the
+                // 36 widths of this q'' is formed once and tested against all six j'.
+                unsigned long long kept_ad[ADA ? NB : 1];
+                if constexpr (ADA) {
+#pragma unroll
+                    for (int j1 = 0; j1 < NB; ++j1) kept_ad[j1] = 0ull;
+#pragma unroll 1
+                    for (int j3 = 0; j3 < NB; ++j3) {
+                        if (!((v3 >> j3) & 1u)) continue;
+                        const int m3 = q3 * NB + j3;
+                        const float4 h3 = t.vp32[m3], l3 = t.vp32lo[m3];
+                        float g32[NB];
+#pragma unroll
+                        for (int j2 = 0; j2 < NB; ++j2)
+                            g32[j2] = a.ad_c32 * vel_diff_norm32(t.vp32[q2 * NB + j2], t.vp32lo[q2 * NB + j2], h3, l3);
+#pragma unroll
+                        for (int j1 = 0; j1 < NB; ++j1) {
+                            if (!((vm1 >> j1) & 1u)) continue;
+                            unsigned row = 0;
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2) {
+                                if (!((v2 >> j2) & 1u)) continue;
+                                const float ad = fabsf((base32[j1] + w2f[j2]) - w3f[j3]);
+                                const int w = window_adaptive32(a, ad, g32[j2]);
+                                if (w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2,
+                                                                                 m3, q2 * NB + j2, m3)))
+                                    row |= 1u << j2;
+                            }
+                            kept_ad[j1] |= (unsigned long long)row << (NB * j3);
+                        }
+                    }
+                }
 #pragma unroll 1
                 for (int j1 = 0; j1 < NB; ++j1) {
                     if (!((vm1 >> j1) & 1u)) continue;
@@ -230,13 +262,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         okj &= cm;
                     }
                     const unsigned long long tri_bits = (unsigned long long)tri << 36;
-                    if constexpr (ADA) {                         // σ per (λ'', λ'''): out-of-line rows
+                    if constexpr (ADA) {
                         unsigned long long kept = 0;
-                        for (int j3 = 0; j3 < NB; ++j3)
-                            if ((v3 >> j3) & 1u)
-                                kept |= (unsigned long long)window_adaptive4_row<NB>(
-                                            t, a, ch, s2, b, m0, q1 * NB + j1, q2, q3 * NB + j3, v2)
-                                        << (NB * j3);
+#pragma unroll
+                        for (int jj = 0; jj < NB; ++jj)
+                            if (jj == j1) kept = kept_ad[jj];
                         kept &= okj;
                         if (kept)
                             ent[n_ent++] = ((unsigned long long)(ix - qb) << 48) |

@@ -3,6 +3,8 @@ they were computed from (so that a test injects the same ω bits and eigenvector
 
   config2_8cubed.npz   seed-0 Morse diamond, 8x8x8 mesh, fixed σ = 0.1 THz, the 8 q points
                        numpy default_rng(0).choice(512, 8) (sorted) x 6 branches, T = 300 K and 700 K
+  mesh12_chunks.npz    seed-0 Morse diamond, 12x12x12 mesh (1728 q: more partner points than one
+                       chunk of the kernels' q'' lists), fixed σ = 0.02 THz, T = 300 K, 4 modes
   config3_16cubed.npz  seed-1 Morse diamond, 16x16x16 mesh, adaptive σ (scale 1), T = 300 K, the
                        first q point of default_rng(1).choice(4096, 145) (sorted) x 6 branches
 
@@ -13,6 +15,7 @@ are called.  Run from the repository root (OpenMP over modes; the 16^3 case take
 one core per mode):
 
     python tests/golden/make_config_goldens.py config2
+    python tests/golden/make_config_goldens.py mesh12
     python tests/golden/make_config_goldens.py config3
 """
 import os
@@ -29,6 +32,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CASES = {
     "config2": dict(seed=0, n=8, k=8, sample_seed=0, take=8, sigma=0.1, adaptive=False,
                     temps=(300.0, 700.0), out="config2_8cubed.npz"),
+    "mesh12": dict(seed=0, n=12, k=2, sample_seed=12, take=2, sigma=0.02, adaptive=False,
+                   temps=(300.0,), out="mesh12_chunks.npz", branches=(1, 5)),
     "config3": dict(seed=1, n=16, k=145, sample_seed=1, take=1, sigma=1.0, adaptive=True,
                     temps=(300.0,), out="config3_16cubed.npz"),
 }
@@ -43,7 +48,8 @@ def run(name):
     N = c["n"] ** 3
     q = sample_q(N, c["k"], c["sample_seed"])[:c["take"]]
     nb = sysm[0].nb
-    modes = np.array([qq * nb + j for qq in q for j in range(nb)], np.int32)
+    branches = c.get("branches", range(nb))
+    modes = np.array([qq * nb + j for qq in q for j in branches], np.int32)
     base = oracle.Problem(*sysm, mesh, T=c["temps"][0], sigma=c["sigma"], sigma_adaptive=c["adaptive"])
     gs, wps, cnts = [], [], []
     for T in c["temps"]:

@@ -263,6 +263,20 @@ fc4_status fc4_set_mode_chunk(fc4_ctx *ctx, int modes_per_chunk, long long w_lim
  * chunk of the last fc4_rates call. */
 fc4_status fc4_memory(const fc4_ctx *ctx, long long out[5]);
 
+/* fc4_set_sampling - sampling estimate of the four-phonon sums for later fc4_rates and
+ * fc4_processes calls (the paper names combining the GPU path with sampling estimation as future
+ * work, Introduction and end of Results, without a scheme; this is the reading implemented).
+ * Each partner pair (λ, q', q'') enters the 4ph sums independently with probability `fraction`:
+ * it is taken iff SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014) of
+ * seed + (key + 1) * 0x9e3779b97f4a7c15, key = (mode * N + q') * N + q'' (64-bit wrap-around), is
+ * below floor(fraction * 2^64).  Γ and WP of the 4ph channels are multiplied by 2^64 / that
+ * threshold, the inverse inclusion probability (an unbiased estimate of the full sums); counts
+ * report the kept processes of the sampled pairs.  Skipped pairs cost no evaluation.  fraction
+ * >= 1 (the default) takes every pair; fraction in (0, 1) samples; other values return
+ * FC4_ERR_INVALID.  Three-phonon channels are never sampled.  fc4_rates_backward refuses
+ * (FC4_ERR_STATE) while sampling is on. */
+fc4_status fc4_set_sampling(fc4_ctx *ctx, double fraction, unsigned long long seed);
+
 /* fc4_set_precision - change the arithmetic of later fc4_rates calls (any fc4_precision; the
  * tables of every mode are built at fc4_init).  Kept sets do not depend on it. */
 fc4_status fc4_set_precision(fc4_ctx *ctx, int precision);
@@ -328,6 +342,13 @@ fc4_status fc4_irreducible_q(const int mesh[3], int n_ops, const int *rot, int f
  * irreducible points, copied to the host); full: host [n_sets][N nb]. */
 fc4_status fc4_expand_irreducible(const int mesh[3], int nb, const int *rep, const double *omega,
                                   double deg_tol, int n_sets, const double *sub, double *full);
+
+/* fc4_device_peaks - calibration of the current device's CUDA cores (no context): out[0] the FP32
+ * and out[1] the FP64 fused multiply-add rate in TFLOP/s (2 flops per FMA), each timed with CUDA
+ * events on `stream` over one launch of 8 x 256-thread blocks per SM running 8 independent FMA
+ * chains per thread, after a warm-up launch.  The rate kernels' arithmetic runs on these units,
+ * so these are the denominators of their roofline.  Synchronises the stream. */
+fc4_status fc4_device_peaks(double out[2], void *stream);
 
 /* fc4_last_error - message of the last failed call on ctx (or, when ctx is NULL, of the last
  * failed fc4_init or host-only call).  The string lives until the next call on ctx. */

@@ -85,8 +85,10 @@ def load(build_if_missing: bool = False):
         "fc4_set_block_threads": [vp, i],
         "fc4_set_tensor_cores": [vp, i],
         "fc4_set_precision": [vp, i],
+        "fc4_set_sampling": [vp, d, ctypes.c_ulonglong],
         "fc4_set_mode_chunk": [vp, i, ll],
         "fc4_memory": [vp, vp],
+        "fc4_device_peaks": [vp, vp],
         "fc4_check_device": [vp],
         "fc4_symmetry_ops": [ctypes.POINTER(_Crystal), ctypes.POINTER(_IFC), ctypes.POINTER(_IFC),
                              ctypes.POINTER(_IFC), d, i, vp, vp, vp],
@@ -103,6 +105,16 @@ def load(build_if_missing: bool = False):
     lib.fc4_destroy.restype = None
     _LIB = lib
     return lib
+
+
+def device_peaks(stream=None) -> dict:
+    """Measured FP32 and FP64 FMA rates (TFLOP/s) of the current device (fc4_device_peaks)."""
+    lib = load()
+    out = np.zeros(2)
+    st = lib.fc4_device_peaks(_ptr(out), _stream(stream))
+    if st != 0:
+        raise FC4Error(st, "fc4_device_peaks failed")
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1])}
 
 
 def _np(x, dt):
@@ -213,6 +225,11 @@ class Engine:
         """Arithmetic of later rates calls (FP64, MIXED, TF32X3, BF16, BF16X3, FP16X3)."""
         self._check(self.lib.fc4_set_precision(self.ctx, int(precision)))
         self.precision = int(precision)
+
+    def set_sampling(self, fraction: float = 1.0, seed: int = 0):
+        """Sampling estimate of the 4ph sums: each partner pair (λ, q', q'') taken with probability
+        ``fraction`` (counter-based hash with ``seed``), sums scaled by the inverse probability."""
+        self._check(self.lib.fc4_set_sampling(self.ctx, float(fraction), int(seed) & 0xFFFFFFFFFFFFFFFF))
 
     def set_mode_chunk(self, modes_per_chunk: int = 0, w_limit_bytes: int = 0):
         """Modes per chunk of a rates call (0: all modes at once, 1: mode by mode) and the cap of

@@ -88,6 +88,9 @@ struct fc4_ctx {
     int mode_chunk = 0;                    // modes per chunk of a rates call (0: as many as W allows)
     size_t w_limit = 0;                    // cap of the W buffer in bytes (0: max(4 GiB, HBM / 4))
     int last_chunk = 0;                    // modes per chunk of the last rates call
+    // sampling estimate of the 4ph sums (fc4_set_sampling); every pair by default
+    int sample_all = 1;
+    unsigned long long sample_threshold = ~0ull, sample_seed = 0;
     std::vector<int> w_modes;
     int *perm4_dev = nullptr;              // device cluster slot -> input index (gradients)
     double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
@@ -281,6 +284,10 @@ void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_
     a.err = c->dev_err;
     a.n_kernels = const_cast<long long *>(&c->n_launches);
     a.tri = (c->sym23 ? 1 : 0) | (c->sym12 && !adaptive ? 2 : 0);
+    a.sample_all = c->sample_all;
+    a.sample_threshold = c->sample_threshold;
+    a.sample_seed = c->sample_seed;
+    a.sample_scale = c->sample_all ? 1.0 : std::ldexp(1.0, 64) / (double)c->sample_threshold;
     if (!adaptive) {
         const double sigma = 2.0 * kPi * sigma_value;
         a.two_sigma = 2.0 * sigma;
@@ -902,6 +909,9 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!c->have_last) return fail(c, FC4_ERR_STATE, "fc4_rates_backward before fc4_rates");
     if (c->t.n_atoms > 2) return fail(c, FC4_ERR_INVALID, "fc4_rates_backward supports cells of at most 2 atoms");
+    if (!c->sample_all && (c->last_mask & 0b11100))
+        return fail(c, FC4_ERR_STATE, "fc4_rates_backward: the four-phonon sampling estimate has no adjoint "
+                                      "(fc4_set_sampling(ctx, 1, 0) turns it off)");
     const int nm = (int)c->last_modes.size();
     cudaStream_t s = (cudaStream_t)stream;
     if (dphi3 && c->nc3) FC4_CUDA(c, cudaMemsetAsync(dphi3, 0, 27 * (size_t)c->nc3 * sizeof(double), s));
@@ -1038,6 +1048,21 @@ fc4_status fc4_memory(const fc4_ctx *c, long long out[5]) {
     out[2] = (long long)c->wbuf_bytes;
     out[3] = (long long)c->part_cap * 7 * 8;
     out[4] = c->last_chunk;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_sampling(fc4_ctx *c, double fraction, unsigned long long seed) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!(fraction > 0.0) || !std::isfinite(fraction)) return fail(c, FC4_ERR_INVALID, "fraction must be in (0, 1]");
+    if (fraction >= 1.0) {
+        c->sample_all = 1;
+        c->sample_threshold = ~0ull;
+    } else {
+        c->sample_all = 0;
+        c->sample_threshold = (unsigned long long)std::ldexp(fraction, 64);   // floor(f 2^64)
+        if (c->sample_threshold == 0) return fail(c, FC4_ERR_INVALID, "fraction below 2^-64");
+    }
+    c->sample_seed = seed;
     return FC4_OK;
 }
 

@@ -94,6 +94,11 @@ struct RateArgs {
     int *err;                    // device flag set by a kernel whose wait expired (may be NULL)
     long long *n_kernels;        // host counter of kernels launched (may be NULL; never read on device)
     int out_ld;                  // row stride of the reduction's outputs [5][out_ld] (0: n_modes)
+    // sampling estimate of the 4ph sums: pair (mode, q', q'') taken iff its SplitMix64 hash <
+    // sample_threshold (sample_all: every pair); the reduction scales the 4ph sums by sample_scale
+    int sample_all;
+    unsigned long long sample_threshold, sample_seed;
+    double sample_scale;
     int tri;                     // triangular 4ph domain allowed: bit 0 +- (Φ4 symmetric in legs 2, 3),
                                  // bit 1 ++ and -- (legs 1, 2; fixed σ only)
 };

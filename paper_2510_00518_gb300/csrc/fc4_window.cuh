@@ -61,6 +61,19 @@ __device__ __forceinline__ float gauss_adaptive32(const Tables &t, const RateArg
     return __expf(-(r * r)) * (kInvSqrtPiF * rs);
 }
 
+// Sampling estimate of the four-phonon sums (fc4_set_sampling): the partner pair (λ, q', q'')
+// enters with probability f, decided by SplitMix64's output function (Steele, Lea and Flood,
+// OOPSLA 2014) of the counter seed + (key + 1) x 0x9e3779b97f4a7c15, key = (mode N + q') N + q'';
+// the pair is in the sample iff the hash is below floor(f 2^64).
+__device__ __forceinline__ bool pair_sampled(const RateArgs &a, int m0, int q1, int q2, int N) {
+    const unsigned long long key = ((unsigned long long)m0 * (unsigned long long)N + (unsigned long long)q1) *
+                                       (unsigned long long)N + (unsigned long long)q2;
+    unsigned long long z = a.sample_seed + (key + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return (z ^ (z >> 31)) < a.sample_threshold;
+}
+
 // Window row of one (q'', λ''') for the four-phonon channels with adaptive σ: bit j'' set iff kept.
 template <int NB>
 static __device__ __noinline__ unsigned window_adaptive4_row(const Tables &t, const RateArgs &a, int ch, int s2,

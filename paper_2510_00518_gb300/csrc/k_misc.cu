@@ -264,6 +264,7 @@ struct int5 { int a, b, c, d, e; };
 // One warp per (channel, mode): lane l sums q' = l, l + 32, ... in order, then a fixed
 // butterfly; Γ = C / N^k * Σ, WP = Σ / N^k (k = 1 for 3ph, 2 for 4ph).
 __global__ void reduce_kernel(int n_modes, int ld, int N, int5 n_part, int channel_mask, double c3, double c4,
+                              double scale4,
                               const double *part_g, const double *part_wp, const long long *part_n,
                               const long long *part_items, const long long *part_ent, const long long *part_ev,
                               const long long *part_cev, double *gamma, double *wp, long long *counts,
@@ -307,6 +308,10 @@ __global__ void reduce_kernel(int n_modes, int ld, int N, int5 n_part, int chann
     if (lane == 0) {
         const double norm = ch < 2 ? (double)N : (double)N * (double)N;
         const double cst = ch < 2 ? c3 : c4;
+        if (ch >= 2 && scale4 != 1.0) {              // sampling estimate: inverse inclusion probability
+            g *= scale4;
+            p *= scale4;
+        }
         // a rate kernel whose bounded wait expired leaves incomplete partials: poison Γ
         if (err && *err) g = __longlong_as_double(0x7ff8000000000000ll);
         gamma[(size_t)ch * ld + ms] = g * cst / norm;
@@ -323,7 +328,8 @@ cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, 
     int5 np;
     np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
     reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        a.n_modes, a.out_ld > 0 ? a.out_ld : a.n_modes, t.N, np, channel_mask, c3, c4, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
+        a.n_modes, a.out_ld > 0 ? a.out_ld : a.n_modes, t.N, np, channel_mask, c3, c4,
+        a.sample_all ? 1.0 : a.sample_scale, a.part_g, a.part_wp, a.part_n, a.part_items, a.part_ent,
         a.part_ev, a.part_cev, gamma, wp, counts, stats, a.err);
     return cudaGetLastError();
 }
@@ -470,7 +476,9 @@ __global__ void processes_kernel(const __grid_constant__ Tables t, const __grid_
         const int q3 = q_index(c0.x + s1 * c1.x + s2 * c2.x, c0.y + s1 * c1.y + s2 * c2.y,
                                c0.z + s1 * c1.z + s2 * c2.z, t.mesh[0], t.mesh[1], t.mesh[2]);
         long long n = 0, o = WRITE ? offsets[i] : 0;
-        if (((t.vmask[q0] >> (m0 - q0 * nb)) & 1u) && ((t.vmask[q1] >> j1) & 1u))
+        // sampling estimate: only the pairs (λ, q', q'') in the sample have processes
+        const bool in_sample = a.sample_all || pair_sampled(a, m0, q1, q2, N);
+        if (in_sample && ((t.vmask[q0] >> (m0 - q0 * nb)) & 1u) && ((t.vmask[q1] >> j1) & 1u))
             for (int j2 = 0; j2 < nb; ++j2) {
                 if (!((t.vmask[q2] >> j2) & 1u)) continue;
                 for (int j3 = 0; j3 < nb; ++j3) {

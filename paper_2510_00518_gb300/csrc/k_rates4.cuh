@@ -92,6 +92,19 @@ __device__ __forceinline__ int tri_code(const RateArgs &a, int ch, int q1, int q
     return q2 < q1 ? -1 : (q2 > q1 ? 1 : 3);
 }
 
+// tri_code of a (q', q'') pair of mode m0 under the sampling estimate: a representative stands for
+// its own pair and, off the diagonal (code 1), for its swapped pair ((λ, q', q''') for +-,
+// (λ, q'', q') for ++ and --); it keeps weight 2 when both are in the sample, becomes weight 1
+// (code 0) when one is, and is skipped (-1) when neither is.
+__device__ __forceinline__ int tri_code_sampled(const RateArgs &a, int ch, int m0, int q1, int q2, int q3, int N) {
+    const int tri = tri_code(a, ch, q1, q2, q3);
+    if (a.sample_all || tri < 0) return tri;
+    const int sa = pair_sampled(a, m0, q1, q2, N) ? 1 : 0;
+    if (tri != 1) return sa ? tri : -1;
+    const int sb = (ch == 3 ? pair_sampled(a, m0, q1, q3, N) : pair_sampled(a, m0, q2, q1, N)) ? 1 : 0;
+    return sa + sb == 2 ? 1 : sa + sb == 1 ? 0 : -1;
+}
+
 // weight of an evaluated process: 2 for a swapped pair, 1 on the diagonal or without symmetry
 __device__ __forceinline__ int tri_weight(int tri, int j1, int j2, int j3) {
     return tri == 0 ? 1 : tri == 1 ? 2 : tri == 2 ? (j2 < j3 ? 2 : 1) : (j2 > j1 ? 2 : 1);
@@ -106,7 +119,7 @@ __device__ __forceinline__ int window_masks(const Tables &t, const RateArgs &a, 
                                             int q3, unsigned (&mask)[NB]) {
     const unsigned v2 = t.vmask[q2], v3 = t.vmask[q3];
     const int q1 = m1 / NB, j1 = m1 - q1 * NB;
-    const int tri = tri_code(a, ch, q1, q2, q3);
+    const int tri = tri_code_sampled(a, ch, m0, q1, q2, q3, t.N);
     if (tri < 0) {
 #pragma unroll
         for (int j3 = 0; j3 < NB; ++j3) mask[j3] = 0u;
@@ -267,7 +280,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                     unsigned mask[NB];
-                    if (tri_code(a, ch, q1, q2, q3) >= 0) acc_cev += NB * NB;   // visited
+                    if (tri_code_sampled(a, ch, m0, q1, q2, q3, N) >= 0) acc_cev += NB * NB;   // visited
                     if (window_masks<NB, ADA>(t, a, ch, s2, base32, m0, m1, w0, w1, q2, q3, mask) > 0) {
                         if constexpr (XROUTE) {
                             unsigned long long e = (unsigned long long)q2 << 40;
@@ -302,7 +315,7 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     const int q3 = q_index(b0 + s2 * c2.x, b1 + s2 * c2.y, b2 + s2 * c2.z,
                                            t.mesh[0], t.mesh[1], t.mesh[2]);
                     unsigned mask[NB];
-                    const int tri = tri_code(a, ch, q1, iq2, q3);
+                    const int tri = tri_code_sampled(a, ch, m0, q1, iq2, q3, N);
                     if constexpr (XROUTE) {
 #pragma unroll
                         for (int j3 = 0; j3 < NB; ++j3) mask[j3] = (unsigned)(e >> (NB * j3)) & ((1u << NB) - 1u);

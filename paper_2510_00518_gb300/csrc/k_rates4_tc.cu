@@ -359,7 +359,7 @@ rates4_tc_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateA
                         w3f[j] = t.om32[q3 * NB + j];
                     }
                     // triangular domain of +- (λ'' <-> λ'''), as in the CUDA-core kernels
-                    tri = tri_code(a, ch, q1, q2, q3);
+                    tri = tri_code_sampled(a, ch, m0, q1, q2, q3, N);
                     unsigned long long okm = 0;
 #pragma unroll
                     for (int j3 = 0; j3 < NB; ++j3)

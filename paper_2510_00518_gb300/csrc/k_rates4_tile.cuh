@@ -199,14 +199,10 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 // is fixed.  One representative of each pair is evaluated with weight 2; a self-paired
                 // point keeps the ordered half of its branch pairs.  The exact window test and the
                 // summand are swap-symmetric, so counts and Γ equal those of the rectangular sum.
-                int tri = 0;           // 0: weight 1; 1: weight 2; 2: +- with q'' = q'''; 3: ++/-- with q'' = q'
-                if (ch == 3 && (a.tri & 1)) {
-                    if (q2 > q3) continue;                       // the swap of (q3, q2)
-                    tri = q2 < q3 ? 1 : 2;
-                } else if (ch != 3 && (a.tri & 2)) {
-                    if (q2 < q1) continue;                       // the swap of (q2, q1)
-                    tri = q2 > q1 ? 1 : 3;
-                }
+                // 0: weight 1; 1: weight 2; 2: +- with q'' = q'''; 3: ++/-- with q'' = q'; -1: the
+                // swap of a pair evaluated elsewhere, or (sampling estimate) a pair outside the sample
+                const int tri = tri_code_sampled(a, ch, m0, q1, q2, q3, N);
+                if (tri < 0) continue;
                 acc_cev += NB * NB * NB;                         // this q'' is visited
                 // (j'', j''') pairs whose two partners both take part: bit NB j''' + j''
                 unsigned long long okm = 0;

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "1", "--cpu-qp", "2", "--cpu-q", "1"],
+                        "--steps", "1", "--warmup", "1", "--cpu-qp", "1", "--cpu-q", "1"],
                        capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -22,7 +22,7 @@ def test_reference_arm_json_line():
               "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["value"] > 0 and d["unit"] == "processes/s" and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "morse-diamond-2atom-8x8x8-all-modes"
+    assert d["config"]["workload"] == "morse-diamond-2atom-16x16x16-145q-adaptive-sigma"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert cb["cpu_model"] and cb["nproc"] >= 1
@@ -36,7 +36,7 @@ def test_one_core_oracle_sample_and_host_info():
     import argparse
     sys.path.insert(0, ROOT)
     import bench
-    args = argparse.Namespace(cpu_qp=8, mesh=8, T=300.0, sigma=0.1)
+    args = argparse.Namespace(cpu_qp=8, mesh=8, workload="allmodes")
     d = bench.cpu_oracle_one_core(args)
     assert d is not None and d["cores"] == 1 and d["value"] > 0 and "q' < 2" in d["sample"]
     model, n = bench.cpu_host_info()

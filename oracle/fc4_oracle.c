@@ -535,3 +535,61 @@ double fc4o_occupation_factor(int ch, double n1, double n2, double n3) {
 }
 
 double fc4o_sigma(const fc4o_problem *p, int ma, int mb) { return sigma_of(p, ma, mb); }
+
+/* ------------------------------------------------------------------ iterative BTE
+ * The paper names solving the linearised Boltzmann equation beyond the RTA as future work
+ * (Results, end); it gives no scheme.  Reading: the ShengBTE / FourPhonon iterative scheme, whose
+ * collision operator reuses the rates' per-process terms.  With F_λ the deviation vector
+ * (n_λ = n0_λ - F_λ . ∇T dn0_λ/dT),
+ *   F_λ = (v_λ + Δ_λ) / Γ_λ,    Δ_λ = Σ_processes γ_p Σ_k s_k (ω_k / ω_λ) F_k,
+ * where γ_p = (C/N^k) w_p |V_p|² is the process's term of Γ_λ (symmetry factor included, so that
+ * Γ_λ = Σ_p γ_p), k runs over the partners of the process, s_k = +1 for a partner on the other
+ * side of the process from λ and -1 for one on the same side:
+ *   3ph+  λ + λ' -> λ''           s = (-1, +1)
+ *   3ph-  λ -> λ' + λ''           s = (+1, +1)
+ *   4ph++ λ + λ' + λ'' -> λ'''    s = (-1, -1, +1)
+ *   4ph+- λ + λ' -> λ'' + λ'''    s = (-1, +1, +1)
+ *   4ph-- λ -> λ' + λ'' + λ'''    s = (+1, +1, +1)
+ * On shell Σ_k s_k ω_k = ω_λ (energy conservation), so a uniform F = u gives Δ_λ = Γ_λ u; with
+ * Gaussian broadening the process's mismatch enters as Σ_k s_k ω_k = ω_λ - Δ_p. */
+static const int bte_sign[5][3] = {{-1, +1, 0}, {+1, +1, 0}, {-1, -1, +1}, {-1, +1, +1}, {+1, +1, +1}};
+
+typedef struct { const double *F; double d[3]; } bte_acc;
+
+static void bte_visit(void *ctx, const fc4o_problem *p, int ch, int m0, int m1, int m2, int m3,
+                      double delta, double sigma, unsigned long long word) {
+    (void)word;
+    bte_acc *a = (bte_acc *)ctx;
+    double w = weight_of(p, ch, m0, m1, m2, m3, delta, sigma);
+    cplx V = v_of(p, ch, m0, m1, m2, m3);
+    double g = w * (V.re * V.re + V.im * V.im);          /* γ_p without C / N^k (applied per mode) */
+    int mk[3] = {m1, m2, m3};
+    int np = (ch < 2) ? 2 : 3;
+    for (int k = 0; k < np; k++) {
+        double xi = p->omega[mk[k]] / p->omega[m0];
+        double c = g * ((double)bte_sign[ch][k] * xi);
+        for (int x = 0; x < 3; x++) a->d[x] += c * a->F[3 * (size_t)mk[k] + x];
+    }
+}
+
+/* Δ_λ [n_modes][3] of the listed modes for the deviation vectors F [nq * nb][3] over the channels
+ * in channel_mask (units of F times ps^-1; the sampling estimate's scale applies as for Γ). */
+int fc4o_bte_offdiag(const fc4o_problem *p, int n_modes, const int *modes, int channel_mask,
+                     const double *F, double *delta) {
+    double N = (double)p->nq;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n_modes; i++) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int ch = 0; ch < 5; ch++) {
+            if (!(channel_mask & (1 << ch))) continue;
+            bte_acc a = {F, {0.0, 0.0, 0.0}};
+            enumerate(p, ch, modes[i], 0, bte_visit, &a);
+            double norm = (ch < 2) ? N : N * N;
+            double cst = (ch < 2) ? p->c3 : p->c4;
+            double scale = (ch < 2 || p->sample_all) ? 1.0 : ldexp(1.0, 64) / (double)p->sample_threshold;
+            for (int x = 0; x < 3; x++) acc[x] += a.d[x] * scale * cst / norm;
+        }
+        for (int x = 0; x < 3; x++) delta[3 * (size_t)i + x] = acc[x];
+    }
+    return 0;
+}

@@ -184,6 +184,37 @@ fc4_status fc4_rates_static(fc4_ctx *ctx, double T_K, double sigma_value, int ch
                             const int *q_subset, int n_q, double *gamma_out, double *wp_out,
                             long long *counts_out, void *stream);
 
+/* ---------------------------------------------------------------- iterative Boltzmann equation
+ * The paper names the solution of the linearised BTE beyond the RTA as future work (Results,
+ * end) without a scheme.  These calls implement the ShengBTE / FourPhonon iterative scheme on the
+ * rates' own per-process terms γ_p (Γ_λ = Σ_p γ_p, symmetry factors included): with the deviation
+ * vectors F_λ (Å; n_λ = n0_λ - F_λ . ∇T dn0_λ/dT),
+ *   F_λ = (v_λ + Δ_λ) / Γ_λ,   Δ_λ = Σ_p γ_p Σ_k s_k (ω_k / ω_λ) F_k,
+ * k over the partners of the process, s_k = +1 for a partner on the other side of the process
+ * from λ and -1 for one on the same side: 3ph+ (-λ', +λ''), 3ph- (+λ', +λ''), 4ph++ (-λ', -λ'',
+ * +λ'''), 4ph+- (-λ', +λ'', +λ'''), 4ph-- (+λ', +λ'', +λ''').  κ_αβ = 1/(N V_cell) Σ_λ C_λ v_λα
+ * F_λβ (W/(m K)); F = v / Γ gives the RTA κ of fc4_kappa.  The matrix elements are recomputed at
+ * every application (no stored scattering matrix), with the same window, triangular domain,
+ * precision and sampling as fc4_rates.  Cells of at most two atoms. */
+
+/* fc4_bte_offdiag - Δ of the modes of q_subset (NULL: all) for deviation vectors F (device
+ * [N nb][3], Å), channels in channel_mask, σ as in fc4_rates: delta_out device [n_q nb][3]
+ * (Å/ps).  It counts as the last rates call for fc4_rates_backward and fc4_processes
+ * (T, σ, mask, subset). */
+fc4_status fc4_bte_offdiag(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_value,
+                           int channel_mask, const int *q_subset, int n_q, const double *F,
+                           double *delta_out, void *stream);
+
+/* fc4_kappa_iterative - iterate F^0 = v / Γ, F^{n+1} = (v + Δ(F^n)) / Γ (Γ_λ = Σ of gamma[ch][λ]
+ * over channel_mask; modes with ω = 0 or Γ <= 0 keep F = 0) until the largest change of a κ
+ * component is at most tol x max |κ| or max_iter applications of Δ were made.  gamma: device
+ * [5][N nb] from fc4_rates over the whole mesh with the same T, σ and mask; kappa_out: device [9]
+ * of the last iterate (W/(m K)); F_out: device [N nb][3] or NULL; *iters_out (host, may be
+ * NULL): the number of Δ applications.  Synchronises the stream once per iteration. */
+fc4_status fc4_kappa_iterative(fc4_ctx *ctx, double T_K, int sigma_adaptive, double sigma_value,
+                               int channel_mask, const double *gamma, int max_iter, double tol,
+                               double *kappa_out, double *F_out, int *iters_out, void *stream);
+
 /* fc4_processes - the kept processes of one mode and channel, as canonical 64-bit words in
  * ascending order (the paper's loop order q', j', then the remaining branches; Algorithm 3):
  *   3ph: word = (q' nb + j') nb + j''

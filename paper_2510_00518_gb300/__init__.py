@@ -86,6 +86,8 @@ def load(build_if_missing: bool = False):
         "fc4_set_tensor_cores": [vp, i],
         "fc4_set_precision": [vp, i],
         "fc4_set_sampling": [vp, d, ctypes.c_ulonglong],
+        "fc4_bte_offdiag": [vp, d, i, d, i, vp, i, vp, vp, vp],
+        "fc4_kappa_iterative": [vp, d, i, d, i, vp, i, d, vp, vp, vp, vp],
         "fc4_set_mode_chunk": [vp, i, ll],
         "fc4_memory": [vp, vp],
         "fc4_device_peaks": [vp, vp],
@@ -343,6 +345,33 @@ class Engine:
         self._check(self.lib.fc4_kappa(self.ctx, float(T), _tptr(g), int(channel_mask), _tptr(out),
                                        _stream(stream)))
         return out.view(3, 3)
+
+    def bte_offdiag(self, T: float, sigma_thz: float, F, channel_mask: int = 31, q_subset=None,
+                    adaptive: bool = False, out=None, stream=None):
+        """Δ [n_modes, 3] of the iterative BTE for deviation vectors F [N nb, 3] (CUDA float64)."""
+        import torch
+        qs = None if q_subset is None else _np(q_subset, np.int32)
+        nm = (self.nq if qs is None else qs.size) * self.nb
+        Fd = F.contiguous().to(torch.float64)
+        if out is None:
+            out = torch.empty((nm, 3), dtype=torch.float64, device=Fd.device)
+        self._check(self.lib.fc4_bte_offdiag(self.ctx, float(T), 1 if adaptive else 0, float(sigma_thz),
+                                             int(channel_mask), None if qs is None else _ptr(qs),
+                                             0 if qs is None else qs.size, _tptr(Fd), _tptr(out), _stream(stream)))
+        return out
+
+    def kappa_iterative(self, T: float, sigma_thz: float, gamma, channel_mask: int = 31, adaptive: bool = False,
+                        max_iter: int = 100, tol: float = 1e-8, stream=None):
+        """(κ 3x3, F [N nb, 3], iterations) of the iterative BTE from Γ [5, N nb] of the whole mesh."""
+        import torch
+        g = gamma.contiguous()
+        k = torch.empty(9, dtype=torch.float64, device=g.device)
+        F = torch.empty((self.nq * self.nb, 3), dtype=torch.float64, device=g.device)
+        it = ctypes.c_int(0)
+        self._check(self.lib.fc4_kappa_iterative(self.ctx, float(T), 1 if adaptive else 0, float(sigma_thz),
+                                                 int(channel_mask), _tptr(g), int(max_iter), float(tol), _tptr(k),
+                                                 _tptr(F), ctypes.byref(it), _stream(stream)))
+        return k.view(3, 3), F, it.value
 
     def kappa_backward(self, T: float, gamma, dL_dkappa, channel_mask: int = 31, out=None, stream=None):
         """dL/dΓ [5, N*nb] from dL/dκ (3x3)."""

@@ -91,6 +91,10 @@ struct fc4_ctx {
     // sampling estimate of the 4ph sums (fc4_set_sampling); every pair by default
     int sample_all = 1;
     unsigned long long sample_threshold = ~0ull, sample_seed = 0;
+    // iterative BTE scratch
+    double *part_d = nullptr, *bte_F = nullptr, *bte_delta = nullptr, *bte_kappa = nullptr;
+    float *bte_F32 = nullptr;
+    size_t part_d_cap = 0;
     std::vector<int> w_modes;
     int *perm4_dev = nullptr;              // device cluster slot -> input index (gradients)
     double *adj_part = nullptr;            // per-mode gradient slices of fc4_rates_backward
@@ -689,9 +693,19 @@ fc4_status fc4_get_modes(fc4_ctx *c, double *omega, double *vel, double *evec) {
     return FC4_OK;
 }
 
-fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value,
-                     int channel_mask, const int *q_subset, int n_q, double *gamma_out,
-                     double *wp_out, long long *counts_out, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// κ's prefactor 1/(N V_cell) with v in Å/ps (x 100 m/s) and 1/Γ in ps (x 1e-12 s): W/(m K)
+double kappa_scale(const fc4_ctx *c) { return 1e4 * 1e-12 / ((double)c->t.N * c->volume * 1e-30); }
+
+// The rates call behind fc4_rates and the iterative BTE: with bte_F set (device [N nb][3]), the
+// kernels also accumulate the BTE's off-diagonal term, reduced into delta_out [n_q nb][3]; Γ, WP
+// and counts are written when gamma_out is set.
+fc4_status rates_call(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value, int channel_mask,
+                      const int *q_subset, int n_q, double *gamma_out, double *wp_out, long long *counts_out,
+                      void *stream, const double *bte_F, double *delta_out) {
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!(T_K > 0.0) || !std::isfinite(T_K)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
     if (sigma_adaptive != 0 && sigma_adaptive != 1) return fail(c, FC4_ERR_INVALID, "sigma_adaptive must be 0 or 1");
@@ -718,7 +732,10 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         c->last_modes.clear();
         return FC4_OK;
     }
-    if (!gamma_out) return fail(c, FC4_ERR_INVALID, "gamma_out is NULL");
+    if (!gamma_out && !bte_F) return fail(c, FC4_ERR_INVALID, "gamma_out is NULL");
+    if (bte_F && (!delta_out || c->t.n_atoms > 2))
+        return fail(c, FC4_ERR_INVALID, bte_F && delta_out ? "the iterative BTE supports cells of at most 2 atoms"
+                                                           : "delta_out is NULL");
     if ((size_t)nm > c->modes_cap) {
         if (c->modes) { cudaFree(c->modes); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->modes)); }
         FC4_CUDA(c, dalloc(c, &c->modes, (size_t)nm));
@@ -755,6 +772,17 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         FC4_CUDA(c, dalloc(c, &c->part_ev, need));
         FC4_CUDA(c, dalloc(c, &c->part_cev, need));
         c->part_cap = need;
+    }
+    if (bte_F) {                          // BTE partials [5][chunk][N][3] and the FP32 copy of F
+        if (3 * need > c->part_d_cap) {
+            if (c->part_d) { cudaFree(c->part_d); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->part_d)); }
+            c->part_d = nullptr;
+            c->part_d_cap = 0;
+            FC4_CUDA(c, dalloc(c, &c->part_d, 3 * need));
+            c->part_d_cap = 3 * need;
+        }
+        if (!c->bte_F32) FC4_CUDA(c, dalloc(c, &c->bte_F32, (size_t)3 * N * nb));
+        FC4_CUDA(c, fc4::launch_to_f32(bte_F, c->bte_F32, (size_t)3 * N * nb, s));
     }
     if (per_mode && c->wbuf_bytes < chunk * per_mode) {     // W scratch of the tiled 4ph path
         if (c->wbuf) {
@@ -794,6 +822,11 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         a.part_cev = c->part_cev;
         a.wbuf = per_mode ? c->wbuf : nullptr;
         a.wbuf_bytes = per_mode ? c->wbuf_bytes : 0;
+        if (bte_F) {
+            a.bte_F = bte_F;
+            a.bte_F32 = c->bte_F32;
+            a.part_d = c->part_d;
+        }
         const std::vector<int> cmodes(modes.begin() + m0, modes.begin() + m0 + cm);
         for (int ch = 0; ch < 5; ++ch) {
             if (!((channel_mask >> ch) & 1)) continue;
@@ -819,9 +852,12 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
         }
         a.out_ld = nm;
         Timed tm(c, 5, s);
-        FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out + m0,
-                                       wp_out ? wp_out + m0 : nullptr, counts_out ? counts_out + m0 : nullptr,
-                                       c->stats, s));
+        if (gamma_out)
+            FC4_CUDA(c, fc4::launch_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), gamma_out + m0,
+                                           wp_out ? wp_out + m0 : nullptr, counts_out ? counts_out + m0 : nullptr,
+                                           c->stats, s));
+        if (bte_F)
+            FC4_CUDA(c, fc4::launch_bte_reduce(c->t, a, channel_mask, unit_c3(), unit_c4(), delta_out + 3 * m0, s));
     }
     for (int k = 0; k < 5; ++k)
         if (!((channel_mask >> k) & 1)) c->ev_used[k] = false;
@@ -835,6 +871,69 @@ fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_va
     c->last_adaptive = sigma_adaptive != 0;
     c->last_mask = channel_mask;
     c->last_modes = modes;
+    return FC4_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fc4_status fc4_rates(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value,
+                     int channel_mask, const int *q_subset, int n_q, double *gamma_out,
+                     double *wp_out, long long *counts_out, void *stream) {
+    return rates_call(c, T_K, sigma_adaptive, sigma_value, channel_mask, q_subset, n_q, gamma_out, wp_out,
+                      counts_out, stream, nullptr, nullptr);
+}
+
+fc4_status fc4_bte_offdiag(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value, int channel_mask,
+                           const int *q_subset, int n_q, const double *F, double *delta_out, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!F || !delta_out) return fail(c, FC4_ERR_INVALID, "F and delta_out are required");
+    return rates_call(c, T_K, sigma_adaptive, sigma_value, channel_mask, q_subset, n_q, nullptr, nullptr, nullptr,
+                      stream, F, delta_out);
+}
+
+fc4_status fc4_kappa_iterative(fc4_ctx *c, double T_K, int sigma_adaptive, double sigma_value, int channel_mask,
+                               const double *gamma, int max_iter, double tol, double *kappa_out, double *F_out,
+                               int *iters_out, void *stream) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (!gamma || !kappa_out) return fail(c, FC4_ERR_INVALID, "gamma and kappa_out are required");
+    if (max_iter < 0 || !(tol >= 0.0)) return fail(c, FC4_ERR_INVALID, "max_iter >= 0 and tol >= 0 required");
+    if (channel_mask < 0 || channel_mask > 31) return fail(c, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
+    if (!(T_K > 0.0) || !std::isfinite(T_K)) return fail(c, FC4_ERR_INVALID, "T must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nm = (size_t)c->t.N * c->t.nb;
+    if (!c->bte_F) FC4_CUDA(c, dalloc(c, &c->bte_F, 3 * nm));
+    if (!c->bte_delta) FC4_CUDA(c, dalloc(c, &c->bte_delta, 3 * nm));
+    if (!c->bte_F32) FC4_CUDA(c, dalloc(c, &c->bte_F32, 3 * nm));
+    if (!c->bte_kappa) FC4_CUDA(c, dalloc(c, &c->bte_kappa, 9));
+    const double xw = kHbar * 1e12 / (kKb * T_K);
+    FC4_CUDA(c, fc4::launch_bte_update(c->t, gamma, channel_mask, nullptr, c->bte_F, c->bte_F32, s));   // F = v / Γ
+    FC4_CUDA(c, fc4::launch_kappa_F(c->t, xw, kKb, c->bte_F, kappa_scale(c), c->bte_kappa, s));
+    double kp[9], kn[9];
+    FC4_CUDA(c, cudaMemcpyAsync(kp, c->bte_kappa, sizeof kp, cudaMemcpyDeviceToHost, s));
+    FC4_CUDA(c, cudaStreamSynchronize(s));
+    int it = 0;
+    for (it = 1; it <= max_iter; ++it) {
+        fc4_status st = rates_call(c, T_K, sigma_adaptive, sigma_value, channel_mask, nullptr, 0, nullptr, nullptr,
+                                   nullptr, stream, c->bte_F, c->bte_delta);
+        if (st != FC4_OK) return st;
+        FC4_CUDA(c, fc4::launch_bte_update(c->t, gamma, channel_mask, c->bte_delta, c->bte_F, c->bte_F32, s));
+        FC4_CUDA(c, fc4::launch_kappa_F(c->t, xw, kKb, c->bte_F, kappa_scale(c), c->bte_kappa, s));
+        FC4_CUDA(c, cudaMemcpyAsync(kn, c->bte_kappa, sizeof kn, cudaMemcpyDeviceToHost, s));
+        FC4_CUDA(c, cudaStreamSynchronize(s));
+        double dmax = 0.0, kmax = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            dmax = std::max(dmax, std::fabs(kn[k] - kp[k]));
+            kmax = std::max(kmax, std::fabs(kn[k]));
+        }
+        std::memcpy(kp, kn, sizeof kp);
+        if (dmax <= tol * kmax) break;
+    }
+    if (it > max_iter) it = max_iter;
+    FC4_CUDA(c, cudaMemcpyAsync(kappa_out, c->bte_kappa, 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (F_out) FC4_CUDA(c, cudaMemcpyAsync(F_out, c->bte_F, 3 * nm * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (iters_out) *iters_out = it;
     return FC4_OK;
 }
 
@@ -878,7 +977,6 @@ fc4_status fc4_processes(fc4_ctx *c, int channel, int mode, unsigned long long *
 }
 
 // Σ C v v τ / (N V): v Å/ps -> m/s (1e2)², τ ps -> s (1e-12), V Å³ -> m³ (1e-30)
-static double kappa_scale(const fc4_ctx *c) { return 1e4 * 1e-12 / ((double)c->t.N * c->volume * 1e-30); }
 
 fc4_status fc4_kappa(fc4_ctx *c, double T_K, const double *gamma, int channel_mask, double *kappa_out,
                      void *stream) {

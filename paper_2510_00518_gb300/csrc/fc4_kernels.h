@@ -99,6 +99,11 @@ struct RateArgs {
     int sample_all;
     unsigned long long sample_threshold, sample_seed;
     double sample_scale;
+    // iterative BTE: with part_d set, the kernels also accumulate Σ_p γ_p Σ_k s_k ω_k F_k / ω_λ
+    // into part_d [5][n_modes][N][3] for the deviation vectors F [N nb][3]
+    const double *bte_F;
+    const float *bte_F32;
+    double *part_d;
     int tri;                     // triangular 4ph domain allowed: bit 0 +- (Φ4 symmetric in legs 2, 3),
                                  // bit 1 ++ and -- (legs 1, 2; fixed σ only)
 };
@@ -114,6 +119,14 @@ cudaError_t launch_rates4_tc(const Tables &t, const RateArgs &a, int ch, int mod
                              cudaStream_t s);
 // bytes of W scratch the tiled 4ph path needs per mode (0 if the general kernel is used)
 size_t rates4_wbuf_per_mode(const Tables &t, int fp64);
+// iterative BTE: Δ [n_modes][3] from part_d (fixed order), F = v / Γ, F = (v + Δ) / Γ, κ from F
+cudaError_t launch_bte_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3, double c4,
+                              double *delta, cudaStream_t s);
+cudaError_t launch_bte_update(const Tables &t, const double *gamma, int mask, const double *delta, double *F,
+                              float *F32, cudaStream_t s);
+cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_kappa_F(const Tables &t, double hbar_over_kT, double kB, const double *F, double scale,
+                           double *kappa, cudaStream_t s);
 cudaError_t launch_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3,
                           double c4, double *gamma, double *wp, long long *counts,
                           unsigned long long *stats, cudaStream_t s);

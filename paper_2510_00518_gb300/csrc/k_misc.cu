@@ -513,3 +513,108 @@ cudaError_t launch_write_processes(const Tables &t, const RateArgs &a, int ch, i
 }
 
 }  // namespace fc4
+
+// ------------------------------------------------------------------------------ iterative BTE
+
+namespace fc4 {
+
+// Δ[ms][x] = Σ_ch (C_ch / N^k_ch) s_ch Σ_q' part_d[ch][ms][q'][x], one warp per (mode, x); the
+// partial slots are summed in a fixed order (lane stride, then a fixed shuffle tree).
+__global__ void bte_reduce_kernel(int n_modes, int N, int5 n_part, int channel_mask, double c3, double c4,
+                                  double scale4, const double *part_d, double *delta) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= 3 * n_modes) return;
+    const int ms = w / 3, x = w - 3 * ms;
+    double tot = 0.0;
+    for (int ch = 0; ch < 5; ++ch) {
+        if (!((channel_mask >> ch) & 1)) continue;
+        const int np = ch == 0 ? n_part.a : ch == 1 ? n_part.b : ch == 2 ? n_part.c : ch == 3 ? n_part.d : n_part.e;
+        const size_t base = ((size_t)ch * n_modes + ms) * N;
+        double d = 0.0;
+        for (int q = lane; q < np; q += 32) d += part_d[3 * (base + q) + x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+        const double norm = ch < 2 ? (double)N : (double)N * (double)N;
+        const double cst = ch < 2 ? c3 : c4;
+        if (ch >= 2) d *= scale4;
+        tot += d * cst / norm;
+    }
+    if (lane == 0) delta[3 * (size_t)ms + x] = tot;
+}
+
+cudaError_t launch_bte_reduce(const Tables &t, const RateArgs &a, int channel_mask, double c3, double c4,
+                              double *delta, cudaStream_t s) {
+    const long long threads = 32LL * 3 * a.n_modes;
+    if (threads == 0) return cudaSuccess;
+    int5 np;
+    np.a = a.n_part[0]; np.b = a.n_part[1]; np.c = a.n_part[2]; np.d = a.n_part[3]; np.e = a.n_part[4];
+    bte_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        a.n_modes, t.N, np, channel_mask, c3, c4, a.sample_all ? 1.0 : a.sample_scale, a.part_d, delta);
+    return cudaGetLastError();
+}
+
+// F = (v + Δ) / Γ_tot for modes with ω > 0 and Γ_tot > 0, else 0 (Δ = NULL: the RTA start v / Γ);
+// F32 receives the FP32 copy the mixed-precision kernels read.
+__global__ void bte_update_kernel(int nm, const double *om, const double *vel, const double *gamma, int mask,
+                                  const double *delta, double *F, float *F32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    const double g = gamma_total(gamma, nm, mask, i);
+    const bool ok = om[i] > 0.0 && g > 0.0;
+    for (int x = 0; x < 3; ++x) {
+        const double f = ok ? (vel[3 * (size_t)i + x] + (delta ? delta[3 * (size_t)i + x] : 0.0)) / g : 0.0;
+        F[3 * (size_t)i + x] = f;
+        F32[3 * (size_t)i + x] = (float)f;
+    }
+}
+
+cudaError_t launch_bte_update(const Tables &t, const double *gamma, int mask, const double *delta, double *F,
+                              float *F32, cudaStream_t s) {
+    const int nm = t.N * t.nb;
+    bte_update_kernel<<<(nm + 255) / 256, 256, 0, s>>>(nm, t.om, t.vel, gamma, mask, delta, F, F32);
+    return cudaGetLastError();
+}
+
+__global__ void to_f32_kernel(const double *in, float *out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// κ_ab = scale Σ_λ C_λ v_a F_b over modes with ω > 0 (one block, fixed-order sums).
+__global__ void __launch_bounds__(256)
+kappa_F_kernel(int nm, const double *om, const double *vel, double x_per_w, double kB, const double *F,
+               double scale, double *kappa) {
+    __shared__ double s_red[32];
+    double acc[9];
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+        const double w = om[i];
+        if (!(w > 0.0)) continue;
+        const double x = w * x_per_w;
+        const double n = 1.0 / expm1(x);
+        const double c = kB * x * x * n * (n + 1.0);
+        const double *v = vel + 3 * (size_t)i;
+        const double *f = F + 3 * (size_t)i;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) acc[3 * a + b] += c * v[a] * f[b];
+    }
+    for (int k = 0; k < 9; ++k) {
+        const double r = block_sum(acc[k], s_red);
+        if (threadIdx.x == 0) kappa[k] = r * scale;
+    }
+}
+
+cudaError_t launch_kappa_F(const Tables &t, double hbar_over_kT, double kB, const double *F, double scale,
+                           double *kappa, cudaStream_t s) {
+    kappa_F_kernel<<<1, 256, 0, s>>>(t.N * t.nb, t.om, t.vel, hbar_over_kT, kB, F, scale, kappa);
+    return cudaGetLastError();
+}
+
+}  // namespace fc4

@@ -37,6 +37,7 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const int m0 = a.modes[ms];
     const int q0 = m0 / NB, j0 = m0 - q0 * NB;
     double acc_g = 0.0, acc_wp = 0.0;
+    double acc_d[3] = {0.0, 0.0, 0.0};         // iterative BTE (a.part_d set): Σ γ Σ_k s_k ω_k F_k
     long long acc_n = 0;
     if (!(q0 == 0 && j0 < 3)) {
         const int4 c0 = t.qc[q0];
@@ -128,6 +129,12 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
                     acc_wp += w;
                     acc_g += w * (V.x * V.x + V.y * V.y);
                     acc_n += 1;
+                    if (a.part_d) {                    // partner signs: 3ph+ (-, +), 3ph- (+, +)
+                        const double gp = w * (V.x * V.x + V.y * V.y);
+                        const double o1 = (ch == 0 ? -1.0 : 1.0) * t.om[m1], o2 = t.om[m2];
+                        for (int x = 0; x < 3; ++x)
+                            acc_d[x] += gp * (o1 * a.bte_F[3 * m1 + x] + o2 * a.bte_F[3 * m2 + x]);
+                    }
                 }
                 __syncthreads();                               // sList reused next
             }
@@ -136,8 +143,13 @@ rates3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     const double g = block_sum(acc_g, s_red);
     const double wp = block_sum(acc_wp, s_red);
     const long long n = block_sum(acc_n, s_redn);
+    double dsum[3] = {0.0, 0.0, 0.0};
+    if (a.part_d)
+        for (int x = 0; x < 3; ++x) dsum[x] = block_sum(acc_d[x], s_red);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N;   // one partial slot per mode
+        if (a.part_d)
+            for (int x = 0; x < 3; ++x) a.part_d[3 * o + x] = dsum[x] * t.invw[m0];
         a.part_g[o] = g;
         a.part_wp[o] = wp;
         a.part_n[o] = n;

@@ -28,6 +28,8 @@ struct Sel {
     static __device__ __forceinline__ const R *ism4(const Tables &t);
     static __device__ __forceinline__ const R *occ(const Tables &t);
     static __device__ __forceinline__ const R *invw(const Tables &t);
+    static __device__ __forceinline__ const R *om(const Tables &t);
+    static __device__ __forceinline__ const R *bteF(const RateArgs &a);
 };
 template <> struct Sel<double> {
     static __device__ __forceinline__ const double2 *ev(const Tables &t) { return t.ev; }
@@ -37,6 +39,8 @@ template <> struct Sel<double> {
     static __device__ __forceinline__ const double *ism4(const Tables &t) { return t.c4_ism; }
     static __device__ __forceinline__ const double *occ(const Tables &t) { return t.occ; }
     static __device__ __forceinline__ const double *invw(const Tables &t) { return t.invw; }
+    static __device__ __forceinline__ const double *om(const Tables &t) { return t.om; }
+    static __device__ __forceinline__ const double *bteF(const RateArgs &a) { return a.bte_F; }
 };
 template <> struct Sel<float> {
     static __device__ __forceinline__ const float2 *ev(const Tables &t) { return t.ev32; }
@@ -46,6 +50,8 @@ template <> struct Sel<float> {
     static __device__ __forceinline__ const float *ism4(const Tables &t) { return t.c4_ism32; }
     static __device__ __forceinline__ const float *occ(const Tables &t) { return t.occ32; }
     static __device__ __forceinline__ const float *invw(const Tables &t) { return t.invw32; }
+    static __device__ __forceinline__ const float *om(const Tables &t) { return t.om32; }
+    static __device__ __forceinline__ const float *bteF(const RateArgs &a) { return a.bte_F32; }
 };
 
 // Exact FP64 decision for the rare candidates inside the prefilter's ambiguity band (kept out of
@@ -496,5 +502,7 @@ cudaError_t launch4_tile_f(int na, const Tables &t, const RateArgs &a, int ch, c
 cudaError_t launch4_tile_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
 cudaError_t launch4_tile_ad_f(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
 cudaError_t launch4_tile_ad_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
+cudaError_t launch4_tile_bte_f(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
+cudaError_t launch4_tile_bte_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
 
 }  // namespace fc4

@@ -25,6 +25,11 @@ cudaError_t launch_rates4(const Tables &t, RateArgs &a, int ch, int fp64, int th
     const int na = t.n_atoms;
     const size_t per_mode = rates4_wbuf_per_mode(t, fp64);
     const bool ad = a.adaptive != 0;
+    if (a.part_d) {                        // iterative BTE: the tiled kernels only
+        if (!(per_mode && a.wbuf && a.wbuf_bytes >= per_mode)) return cudaErrorInvalidValue;
+        a.n_part[ch] = t.N;
+        return fp64 ? launch4_tile_bte_d(na, t, a, ch, s) : launch4_tile_bte_f(na, t, a, ch, s);
+    }
     if (per_mode && a.wbuf && a.wbuf_bytes >= per_mode) {
         a.n_part[ch] = t.N;
         if (ad) return fp64 ? launch4_tile_ad_d(na, t, a, ch, s) : launch4_tile_ad_f(na, t, a, ch, s);

@@ -105,7 +105,10 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
     }
 }
 
-template <typename R, int NA, bool ADA, int kQPT>
+// BTE = true also accumulates the off-diagonal term of the iterative Boltzmann equation,
+//   Δ_λ = Σ_p γ_p Σ_k s_k (ω_k / ω_λ) F_k  (partner signs: ++ (-, -, +), +- (-, +, +), -- (+, +, +)),
+// into a.part_d; the partner combination is symmetric under the swap the triangular domain uses.
+template <typename R, int NA, bool ADA, int kQPT, bool BTE = false>
 __global__ void __launch_bounds__(kTileQ, 4)
 rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
                    int mode0, const Cplx<R> *__restrict__ wall) {
@@ -120,7 +123,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     C *sW = reinterpret_cast<C *>(smem);                        // [NB][nk][9]
     unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB * kQPT]
     __shared__ int s_scan[32];
-    __shared__ double s_red[2 * 32];
+    __shared__ double s_red[(BTE ? 5 : 2) * 32];
     __shared__ long long s_redn[5 * 32];
     __shared__ unsigned short s_tri[kTriChunk];                 // +- triangle: q'' - chunk start
 
@@ -135,6 +138,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     const R *invw = Sel<R>::invw(t);
 
     Acc<R> acc_g, acc_wp;
+    Acc<R> acc_d[BTE ? 3 : 1];
     long long acc_n = 0, acc_items = 0, acc_ent = 0, acc_ev = 0, acc_cev = 0;
     const unsigned vm1 = t.vmask[q1];
 
@@ -431,6 +435,16 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         acc_g.add(w * (V.x * V.x + V.y * V.y));
                         acc_n += wt;
                         acc_ev += 1;
+                        if constexpr (BTE) {
+                            const R *F = Sel<R>::bteF(a);
+                            const R g = w * (V.x * V.x + V.y * V.y);
+                            const R o1 = (R)(ch == 4 ? 1 : -1) * Sel<R>::om(t)[m1];
+                            const R o2 = (R)(ch == 2 ? -1 : 1) * Sel<R>::om(t)[m2];
+                            const R o3 = Sel<R>::om(t)[m3];
+#pragma unroll
+                            for (int x = 0; x < 3; ++x)
+                                acc_d[x].add(g * ((o1 * F[3 * m1 + x] + o2 * F[3 * m2 + x]) + o3 * F[3 * m3 + x]));
+                        }
                     }
                 }
             }
@@ -438,11 +452,22 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
           }
         }
     }
-    double sums[2] = {acc_g.value(), acc_wp.value()};
+    double sums[BTE ? 5 : 2];
+    sums[0] = acc_g.value();
+    sums[1] = acc_wp.value();
+    if constexpr (BTE) {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) sums[2 + x] = acc_d[x].value();
+    }
     long long cnts[5] = {acc_n, acc_items, acc_ent, acc_ev, acc_cev};
-    block_sum_multi<2, 5>(sums, cnts, s_red, s_redn);
+    block_sum_multi<BTE ? 5 : 2, 5>(sums, cnts, s_red, s_redn);
     if (threadIdx.x == 0) {
         const size_t o = ((size_t)ch * a.n_modes + ms) * N + q1;
+        if constexpr (BTE) {
+            const double iw0 = t.invw[m0];                      // ξ_k = ω_k / ω_λ
+#pragma unroll
+            for (int x = 0; x < 3; ++x) a.part_d[3 * o + x] = sums[2 + x] * iw0;
+        }
         a.part_g[o] = sums[0];
         a.part_wp[o] = sums[1];
         a.part_n[o] = cnts[0];
@@ -468,13 +493,13 @@ size_t tile_w_bytes_per_mode(const Tables &t) {
 }
 
 // Launch W (global) then the tiled kernel, over mode chunks that fit in the W buffer.
-template <typename R, int NA, bool ADA>
+template <typename R, int NA, bool ADA, bool BTE = false>
 cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_t s) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
     const bool dense = ch == 3;
     const size_t smem = tile_smem_bytes<R, NA>(t, dense ? kQPTDense : kQPTSparse);
-    auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense> : rates4_tile_kernel<R, NA, ADA, kQPTSparse>;
+    auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense, BTE> : rates4_tile_kernel<R, NA, ADA, kQPTSparse, BTE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB + (size_t)t.n_keys * NA * 27);
@@ -493,7 +518,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
             if (e != cudaSuccess) return e;
             if (a.n_kernels) ++*a.n_kernels;
         }
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (sizeof(R) == 4 && !BTE) {
             if (ch == 3 && a.use_tc) {                  // +-: cluster contraction on the tensor cores
                 e = launch_rates4_tc(t, a, ch, m, nm, reinterpret_cast<const float2 *>(a.wbuf), s);
                 if (e != cudaSuccess) return e;

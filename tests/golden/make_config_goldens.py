@@ -5,6 +5,9 @@ they were computed from (so that a test injects the same ω bits and eigenvector
                        numpy default_rng(0).choice(512, 8) (sorted) x 6 branches, T = 300 K and 700 K
   mesh12_chunks.npz    seed-0 Morse diamond, 12x12x12 mesh (1728 q: more partner points than one
                        chunk of the kernels' q'' lists), fixed σ = 0.02 THz, T = 300 K, 4 modes
+  bte_3cubed.npz       seed-0 Morse diamond, 3x3x3 mesh, fixed σ = 0.1 THz, T = 300 K: RTA Γ of
+                       every mode and the iterative solution of the linearised BTE (κ of every
+                       iterate, the converged F; oracle.Problem.kappa_iterative, tol 1e-12)
   config3_16cubed.npz  seed-1 Morse diamond, 16x16x16 mesh, adaptive σ (scale 1), T = 300 K, the
                        first q point of default_rng(1).choice(4096, 145) (sorted) x 6 branches
 
@@ -16,6 +19,7 @@ one core per mode):
 
     python tests/golden/make_config_goldens.py config2
     python tests/golden/make_config_goldens.py mesh12
+    python tests/golden/make_config_goldens.py bte
     python tests/golden/make_config_goldens.py config3
 """
 import os
@@ -37,6 +41,20 @@ CASES = {
     "config3": dict(seed=1, n=16, k=145, sample_seed=1, take=1, sigma=1.0, adaptive=True,
                     temps=(300.0,), out="config3_16cubed.npz"),
 }
+
+
+def run_bte():
+    import oracle
+    from synth import morse_system
+    P = oracle.Problem(*morse_system(seed=0), (3, 3, 3), T=300.0, sigma=0.1)
+    t0 = time.time()
+    g, wp, cnt = P.rates()
+    k, F, it, ks = P.kappa_iterative(g.sum(0), tol=1e-12, max_iter=200)
+    print(f"bte: {it} iterations, {time.time() - t0:.0f} s", flush=True)
+    m = P.modes
+    np.savez_compressed(os.path.join(HERE, "bte_3cubed.npz"), mesh=np.array((3, 3, 3), np.int32),
+                        seed=np.int32(0), sigma=np.float64(0.1), T=np.array([300.0]), omega=m.omega,
+                        vel=m.vel, evec=m.evec, gamma=g, kappa=np.array(ks), F=F, iterations=np.int32(it))
 
 
 def run(name):
@@ -70,4 +88,4 @@ def run(name):
 
 if __name__ == "__main__":
     for name in sys.argv[1:] or ["config2"]:
-        run(name)
+        run_bte() if name == "bte" else run(name)

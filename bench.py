@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--irreducible", action="store_true",
                    help="irreducible q-points against the full mesh (see run_irreducible)")
     p.add_argument("--symmetric", action="store_true", help="--irreducible on the unperturbed crystal")
+    p.add_argument("--ablation", action="store_true",
+                   help="modes per chunk (all-modes .. mode-by-mode) and compaction ablations, one JSON line")
     p.add_argument("--cpu-sample", action="store_true",
                    help="only the oracle sample (--cpu-q, --cpu-qp) on the host, one JSON line")
     a = p.parse_args()
@@ -674,6 +676,74 @@ def run_irreducible(args):
                       "timing": "wall clock around synchronised calls; L2 flushed before each step"}))
 
 
+def run_ablation(args):
+    """The paper's strategy comparisons on the synthetic crystals, one JSON line:
+      modes per chunk (all-modes strategy down to mode-by-mode, Algorithm 5; Results): device time
+        of the 8x8x8 all-modes rates step and the device memory the context holds for it;
+      compaction vs none (the divergent GPU-only loop, Algorithm 2; Results): the same step, and one
+        batch of the 16x16x16 adaptive workload, with the window's entries compacted (default) or
+        evaluated by the thread that found them.
+    Device times are CUDA events around each call after one warm-up call, L2 flushed before."""
+    import torch
+    from paper_2510_00518_gb300 import Engine, MIXED
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    reps = max(1, min(args.steps, 3))
+
+    def timed(eng, w, q=None):
+        eng.rates(w["T"], w["sigma"], 31, q_subset=q, adaptive=w["adaptive"])
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            g, _, _ = eng.rates(w["T"], w["sigma"], 31, q_subset=q, adaptive=w["adaptive"])
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts)), g
+
+    w8 = dict(WORKLOADS["allmodes"])
+    w8["name"] = w8["name"].format(n=w8["mesh"])
+    sysm, mesh = system_of(w8)
+    out = {"mode": "ablation", "workload": w8["name"], "precision": "mixed", "steps": reps,
+           "timing": "CUDA events per fc4_rates call after one warm-up call; L2 flushed before each"}
+    strat = []
+    g_ref = None
+    for chunk in (0, 768, 96, 12, 1):
+        eng = Engine(*sysm, mesh, precision=MIXED, timing=True)
+        eng.set_mode_chunk(chunk, 0)
+        ms, g = timed(eng, w8)
+        mem = eng.memory()
+        if g_ref is None:
+            g_ref = g.clone()
+        strat.append({"modes_per_chunk": mem["modes_per_chunk"], "ms": ms, "context_bytes": mem["total"],
+                      "w_buffer_bytes": mem["w_buffer"], "partials_bytes": mem["partials"],
+                      "launches": eng.timings()["launches"], "identical_gamma": bool(torch.equal(g, g_ref))})
+        eng.close()
+    out["modes_per_chunk"] = strat
+    comp = {}
+    for name, w, q in (("8x8x8 all modes", w8, None),
+                       ("16x16x16 adaptive, first 5 sampled q", dict(WORKLOADS["precision"]), None)):
+        if w.get("n_sample"):
+            w["name"] = w["name"].format(n=w["mesh"])
+            q = q_sample(w)[:5]
+        s2, m2 = system_of(w)
+        eng = Engine(*s2, m2, precision=MIXED, timing=True)
+        row = {}
+        for flag in (False, True):
+            eng.set_ablation(flag)
+            ms, g = timed(eng, w, q)
+            t = eng.timings()
+            row["no_compaction" if flag else "compacted"] = {"ms": ms, "kernel_ms": {k: t[k] for k in ("4ph++", "4ph+-", "4ph--")}}
+        eng.close()
+        row["slowdown"] = row["no_compaction"]["ms"] / row["compacted"]["ms"]
+        comp[name] = row
+    out["compaction"] = comp
+    print(json.dumps(out))
+
+
 def run_once(args):
     """A single rates call on the first batch of the workload (profiling helper, no timing)."""
     import torch
@@ -695,6 +765,8 @@ if __name__ == "__main__":
         print(json.dumps({"value": kept / dt, "unit": UNIT, "cores": thr, "seconds": dt, "sample": desc}))
     elif a.irreducible:
         run_irreducible(a)
+    elif a.ablation:
+        run_ablation(a)
     elif a.once:
         run_once(a)
     elif a.batch:

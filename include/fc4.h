@@ -246,7 +246,7 @@ fc4_status fc4_kappa_backward(fc4_ctx *ctx, double T_K, const double *gamma, int
  *   dL/dΦ_c = Σ_processes dL/dΓ C/N^k w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
  * Deterministic (fixed summation order).  dL_dgamma: device [5][n_q*nb]; dphi3: device
  * [nc3][27]; dphi4: device [nc4][81], in the cluster order given to fc4_init (overwritten;
- * either may be NULL to skip that order).  Cells of at most 2 atoms.  Returns FC4_ERR_STATE
+ * either may be NULL to skip that order).  Cells of at most 4 atoms.  Returns FC4_ERR_STATE
  * before any fc4_rates call.  Scratch: n_q*nb*max(27 nc3, 81 nc4) doubles (grown on demand). */
 fc4_status fc4_rates_backward(fc4_ctx *ctx, const double *dL_dgamma, double *dphi3,
                               double *dphi4, void *stream);
@@ -307,6 +307,13 @@ fc4_status fc4_memory(const fc4_ctx *ctx, long long out[5]);
  * FC4_ERR_INVALID.  Three-phonon channels are never sampled.  fc4_rates_backward refuses
  * (FC4_ERR_STATE) while sampling is on. */
 fc4_status fc4_set_sampling(fc4_ctx *ctx, double fraction, unsigned long long seed);
+
+/* fc4_set_ablation - measurement switches of the tiled 4ph kernels (results do not change):
+ * bit 0: no compaction - each thread evaluates the (q'', j') entries its own window test found, as
+ * an uncompacted GPU-only loop does (the paper's Algorithm 2 and its warp divergence, Results),
+ * instead of the block's entries being dealt out to all threads in order.  0 (the default)
+ * restores compaction.  Other bits return FC4_ERR_INVALID. */
+fc4_status fc4_set_ablation(fc4_ctx *ctx, int flags);
 
 /* fc4_set_precision - change the arithmetic of later fc4_rates calls (any fc4_precision; the
  * tables of every mode are built at fc4_init).  Kept sets do not depend on it. */

@@ -86,6 +86,7 @@ def load(build_if_missing: bool = False):
         "fc4_set_tensor_cores": [vp, i],
         "fc4_set_precision": [vp, i],
         "fc4_set_sampling": [vp, d, ctypes.c_ulonglong],
+        "fc4_set_ablation": [vp, i],
         "fc4_bte_offdiag": [vp, d, i, d, i, vp, i, vp, vp, vp],
         "fc4_kappa_iterative": [vp, d, i, d, i, vp, i, d, vp, vp, vp, vp],
         "fc4_set_mode_chunk": [vp, i, ll],
@@ -232,6 +233,10 @@ class Engine:
         """Sampling estimate of the 4ph sums: each partner pair (λ, q', q'') taken with probability
         ``fraction`` (counter-based hash with ``seed``), sums scaled by the inverse probability."""
         self._check(self.lib.fc4_set_sampling(self.ctx, float(fraction), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def set_ablation(self, no_compaction: bool = False):
+        """Measurement switch: evaluate each thread's own window entries without compaction."""
+        self._check(self.lib.fc4_set_ablation(self.ctx, 1 if no_compaction else 0))
 
     def set_mode_chunk(self, modes_per_chunk: int = 0, w_limit_bytes: int = 0):
         """Modes per chunk of a rates call (0: all modes at once, 1: mode by mode) and the cap of

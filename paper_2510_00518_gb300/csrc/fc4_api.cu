@@ -91,6 +91,7 @@ struct fc4_ctx {
     // sampling estimate of the 4ph sums (fc4_set_sampling); every pair by default
     int sample_all = 1;
     unsigned long long sample_threshold = ~0ull, sample_seed = 0;
+    int no_compact = 0;                    // ablation of the entry compaction (fc4_set_ablation)
     // iterative BTE scratch
     double *part_d = nullptr, *bte_F = nullptr, *bte_delta = nullptr, *bte_kappa = nullptr;
     float *bte_F32 = nullptr;
@@ -288,6 +289,7 @@ void set_window(const fc4_ctx *c, fc4::RateArgs &a, bool adaptive, double sigma_
     a.err = c->dev_err;
     a.n_kernels = const_cast<long long *>(&c->n_launches);
     a.tri = (c->sym23 ? 1 : 0) | (c->sym12 && !adaptive ? 2 : 0);
+    a.no_compact = c->no_compact;
     a.sample_all = c->sample_all;
     a.sample_threshold = c->sample_threshold;
     a.sample_seed = c->sample_seed;
@@ -1006,7 +1008,7 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
                               void *stream) {
     if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
     if (!c->have_last) return fail(c, FC4_ERR_STATE, "fc4_rates_backward before fc4_rates");
-    if (c->t.n_atoms > 2) return fail(c, FC4_ERR_INVALID, "fc4_rates_backward supports cells of at most 2 atoms");
+    if (c->t.n_atoms > 4) return fail(c, FC4_ERR_INVALID, "fc4_rates_backward supports cells of at most 4 atoms");
     if (!c->sample_all && (c->last_mask & 0b11100))
         return fail(c, FC4_ERR_STATE, "fc4_rates_backward: the four-phonon sampling estimate has no adjoint "
                                       "(fc4_set_sampling(ctx, 1, 0) turns it off)");
@@ -1161,6 +1163,13 @@ fc4_status fc4_set_sampling(fc4_ctx *c, double fraction, unsigned long long seed
         if (c->sample_threshold == 0) return fail(c, FC4_ERR_INVALID, "fraction below 2^-64");
     }
     c->sample_seed = seed;
+    return FC4_OK;
+}
+
+fc4_status fc4_set_ablation(fc4_ctx *c, int flags) {
+    if (!c) return fail(nullptr, FC4_ERR_INVALID, "ctx is NULL");
+    if (flags & ~1) return fail(c, FC4_ERR_INVALID, "unknown ablation flag");
+    c->no_compact = flags & 1;
     return FC4_OK;
 }
 

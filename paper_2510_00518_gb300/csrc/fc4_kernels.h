@@ -101,6 +101,7 @@ struct RateArgs {
     double sample_scale;
     // iterative BTE: with part_d set, the kernels also accumulate Σ_p γ_p Σ_k s_k ω_k F_k / ω_λ
     // into part_d [5][n_modes][N][3] for the deviation vectors F [N nb][3]
+    int no_compact;              // ablation: evaluate each thread's own window entries (no compaction)
     const double *bte_F;
     const float *bte_F32;
     double *part_d;

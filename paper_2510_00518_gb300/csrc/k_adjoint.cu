@@ -371,7 +371,9 @@ cudaError_t launch_adjoint(const Tables &t, const RateArgs &a, int ch, const dou
     switch (t.n_atoms) {
     case 1: return launch_adj_na<1>(t, a, ch, dLdG, cst, part, s);
     case 2: return launch_adj_na<2>(t, a, ch, dLdG, cst, part, s);
-    default: return cudaErrorInvalidValue;       // cells of more than 2 atoms: not instantiated
+    case 3: return launch_adj_na<3>(t, a, ch, dLdG, cst, part, s);
+    case 4: return launch_adj_na<4>(t, a, ch, dLdG, cst, part, s);
+    default: return cudaErrorInvalidValue;       // cells of more than 4 atoms: not instantiated
     }
 }
 

@@ -122,6 +122,7 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
     extern __shared__ __align__(16) unsigned char smem[];
     C *sW = reinterpret_cast<C *>(smem);                        // [NB][nk][9]
     unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sW + NB * nk * 9);   // [kTileQ * NB * kQPT]
+    float *s_g = reinterpret_cast<float *>(sQ + kTileQ * NB * kQPT);   // adaptive σ: [NB * NB][kTileQ] widths
     __shared__ int s_scan[32];
     __shared__ double s_red[(BTE ? 5 : 2) * 32];
     __shared__ long long s_redn[5 * 32];
@@ -217,36 +218,18 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                         if (tri == 2) row &= (2u << j3) - 1u;    // j'' <= j'''
                         okm |= (unsigned long long)row << (NB * j3);
                     }
-                // Adaptive σ: the width of a pair (λ'', λ''') does not depend on j', so each of the
-                // 36 widths of this q'' is formed once and tested against all six j'.
-                unsigned long long kept_ad[ADA ? NB : 1];
+                // Adaptive σ: the width of a pair (λ'', λ''') does not depend on j', so the 36 widths
+                // of this q'' are formed once, kept in this thread's column of s_g, and tested below
+                // against every j' (branch-free masks as for a fixed σ, rare exact decisions out of line).
                 if constexpr (ADA) {
-#pragma unroll
-                    for (int j1 = 0; j1 < NB; ++j1) kept_ad[j1] = 0ull;
 #pragma unroll 1
                     for (int j3 = 0; j3 < NB; ++j3) {
-                        if (!((v3 >> j3) & 1u)) continue;
                         const int m3 = q3 * NB + j3;
                         const float4 h3 = t.vp32[m3], l3 = t.vp32lo[m3];
-                        float g32[NB];
 #pragma unroll
                         for (int j2 = 0; j2 < NB; ++j2)
-                            g32[j2] = a.ad_c32 * vel_diff_norm32(t.vp32[q2 * NB + j2], t.vp32lo[q2 * NB + j2], h3, l3);
-#pragma unroll
-                        for (int j1 = 0; j1 < NB; ++j1) {
-                            if (!((vm1 >> j1) & 1u)) continue;
-                            unsigned row = 0;
-#pragma unroll
-                            for (int j2 = 0; j2 < NB; ++j2) {
-                                if (!((v2 >> j2) & 1u)) continue;
-                                const float ad = fabsf((base32[j1] + w2f[j2]) - w3f[j3]);
-                                const int w = window_adaptive32(a, ad, g32[j2]);
-                                if (w == 2 || (w == 1 && window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2,
-                                                                                 m3, q2 * NB + j2, m3)))
-                                    row |= 1u << j2;
-                            }
-                            kept_ad[j1] |= (unsigned long long)row << (NB * j3);
-                        }
+                            s_g[(j3 * NB + j2) * kTileQ + threadIdx.x] =
+                                a.ad_c32 * vel_diff_norm32(t.vp32[q2 * NB + j2], t.vp32lo[q2 * NB + j2], h3, l3);
                     }
                 }
 #pragma unroll 1
@@ -263,14 +246,30 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     }
                     const unsigned long long tri_bits = (unsigned long long)tri << 36;
                     if constexpr (ADA) {
-                        unsigned long long kept = 0;
+                        unsigned long long sure = 0, amb = 0;
 #pragma unroll
-                        for (int jj = 0; jj < NB; ++jj)
-                            if (jj == j1) kept = kept_ad[jj];
-                        kept &= okj;
-                        if (kept)
+                        for (int j3 = 0; j3 < NB; ++j3)
+#pragma unroll
+                            for (int j2 = 0; j2 < NB; ++j2) {
+                                const float g = s_g[(j3 * NB + j2) * kTileQ + threadIdx.x];
+                                const float ad = fabsf((b + w2f[j2]) - w3f[j3]);
+                                const int k = NB * j3 + j2;
+                                sure |= (unsigned long long)(ad <= fmaf(a.ad_rlo, g, -a.ad_e0) && g > a.ad_gmin) << k;
+                                amb |= (unsigned long long)(ad <= fmaf(a.ad_rhi, g, a.ad_e0)) << k;
+                            }
+                        sure &= okj;
+                        amb &= okj & ~sure;
+                        while (amb) {                            // rare: exact FP64 σ and Δ
+                            const int k = __ffsll(amb) - 1;
+                            amb &= amb - 1;
+                            const int j3 = k / NB, j2 = k - j3 * NB;
+                            if (window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2, q3 * NB + j3,
+                                                      q2 * NB + j2, q3 * NB + j3))
+                                sure |= 1ull << k;
+                        }
+                        if (sure)
                             ent[n_ent++] = ((unsigned long long)(ix - qb) << 48) |
-                                           ((unsigned long long)j1 << 40) | tri_bits | kept;
+                                           ((unsigned long long)j1 << 40) | tri_bits | sure;
                         continue;
                     }
                     float t2[NB];
@@ -312,7 +311,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
             for (int k = 0; k < n_ent; ++k) sQ[off + k] = ent[k];
             __syncthreads();
 
-            for (int it = threadIdx.x; it < total; it += kTileQ) {
+            // Compacted: the block's entries are dealt out to the threads in order.  With the
+            // ablation flag (a.no_compact) each thread instead evaluates the entries its own window
+            // found, as an uncompacted GPU-only loop would, and warps diverge on their counts.
+            const int it_end = a.no_compact ? off + n_ent : total;
+            for (int it = a.no_compact ? off : threadIdx.x; it < it_end; it += a.no_compact ? 1 : kTileQ) {
                 ++acc_ent;
                 const unsigned long long e = sQ[it];
                 const int ixe = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
@@ -479,10 +482,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
 }
 
 template <typename R, int NA>
-size_t tile_smem_bytes(const Tables &t, int qpt = kQPTSparse) {
+size_t tile_smem_bytes(const Tables &t, int qpt = kQPTSparse, bool adaptive = true) {
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
-    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB * qpt;
+    size_t b = sizeof(C) * ((size_t)NB * t.n_keys * 9) + sizeof(unsigned long long) * (size_t)kTileQ * NB * qpt +
+               (adaptive ? sizeof(float) * (size_t)NB * NB * kTileQ : 0);
     return (b + 15) & ~size_t(15);
 }
 
@@ -498,7 +502,7 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
     const bool dense = ch == 3;
-    const size_t smem = tile_smem_bytes<R, NA>(t, dense ? kQPTDense : kQPTSparse);
+    const size_t smem = tile_smem_bytes<R, NA>(t, dense ? kQPTDense : kQPTSparse, ADA);
     auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense, BTE> : rates4_tile_kernel<R, NA, ADA, kQPTSparse, BTE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -68,3 +68,47 @@ def sharded_rates_kappa_irreducible(engine, T: float, sigma_thz: float, rot=None
     full = expand_irreducible(engine.mesh, nb, rep, engine.get_modes()[0], sub, deg_tol)
     kap = engine.kappa(T, torch.from_numpy(full).to(g.device), channel_mask).reshape(-1).clone()
     return mine, g, allreduce_kappa(kap, group).view(3, 3)
+
+
+def allreduce_grad(d3, d4, group=None):
+    """Sum the per-rank gradients dL/dΦ3 [nc3, 27] and dL/dΦ4 [nc4, 81] over ``group`` (one
+    all-reduce of nc3·27 + nc4·81 doubles; either may be None)."""
+    import torch
+    import torch.distributed as dist
+    parts = [x for x in (d3, d4) if x is not None]
+    if not parts or not (dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1):
+        return d3, d4
+    flat = torch.cat([x.reshape(-1) for x in parts])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    out, o = [], 0
+    for x in (d3, d4):
+        if x is None:
+            out.append(None)
+            continue
+        out.append(flat[o:o + x.numel()].view_as(x))
+        o += x.numel()
+    return out[0], out[1]
+
+
+def sharded_kappa_gradient(engine, T: float, sigma_thz: float, dL_dkappa, channel_mask: int = 31, group=None):
+    """dL/dΦ3, dL/dΦ4 of L = Σ dL_dkappa κ with the modes sharded over the ranks: each rank runs
+    the rates of its q block, the κ all-reduce, its share of the adjoint (dL/dΓ of its own modes
+    through fc4_kappa_backward, then fc4_rates_backward), and one gradient all-reduce.  Returns
+    (κ, dL/dΦ3, dL/dΦ4); every rank gets the totals."""
+    import torch
+    qs, g, kap = sharded_rates_kappa(engine, T, sigma_thz, channel_mask, group)
+    nb = engine.nb
+    full = torch.zeros((5, engine.nq * nb), dtype=torch.float64, device=g.device)
+    if qs.size:
+        full[:, int(qs[0]) * nb:(int(qs[-1]) + 1) * nb] = g
+    dk = torch.as_tensor(dL_dkappa, dtype=torch.float64, device=g.device).reshape(3, 3)
+    dg_full = engine.kappa_backward(T, full, dk, channel_mask)
+    dg = dg_full[:, int(qs[0]) * nb:(int(qs[-1]) + 1) * nb].contiguous() if qs.size else dg_full[:, :0]
+    if qs.size:
+        engine.rates(T, sigma_thz, channel_mask, q_subset=qs)       # the subset the backward reads
+        d3, d4 = engine.backward(dg)
+    else:
+        d3 = torch.zeros((engine.nc3, 27), dtype=torch.float64, device=g.device) if engine.nc3 else None
+        d4 = torch.zeros((engine.nc4, 81), dtype=torch.float64, device=g.device) if engine.nc4 else None
+    d3, d4 = allreduce_grad(d3, d4, group)
+    return kap, d3, d4

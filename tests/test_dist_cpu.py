@@ -127,3 +127,72 @@ def test_two_rank_irreducible_kappa(tmp_path):
     for r in range(world):
         k = np.load(tmp_path / f"ki{r}.npy").reshape(-1)
         assert np.allclose(k, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+
+
+class _OracleGradEngine(_OracleEngine):
+    """Adds the calls of the sharded adjoint: fc4_kappa_backward (dκ/dΓ = -C v v / (N V Γ²) of the
+    oracle's κ) and fc4_rates_backward (the oracle's analytic gradient for the last rates call)."""
+
+    def __init__(self, P):
+        super().__init__(P)
+        self.nc3, self.nc4 = P.phi3.n_clusters, P.phi4.n_clusters
+        self._modes = None
+
+    def rates(self, T, sigma_thz, channel_mask, q_subset=None):
+        qs = np.arange(self.nq) if q_subset is None else np.asarray(q_subset)
+        self._modes = (qs[:, None] * self.nb + np.arange(self.nb)).reshape(-1).astype(np.int32)
+        self._mask = channel_mask
+        return super().rates(T, sigma_thz, channel_mask, q_subset)
+
+    def kappa_backward(self, T, gamma, dk, channel_mask):
+        import oracle
+        P = self.P
+        g = gamma.numpy()
+        tot = sum(g[ch] for ch in range(5) if channel_mask >> ch & 1)
+        C = oracle.heat_capacity(P.modes.omega, T)
+        out = np.zeros_like(g)
+        G = dk.numpy()
+        for m in range(tot.size):
+            if P.modes.omega[m] <= 0 or tot[m] <= 0:
+                continue
+            v = P.modes.vel[m] * 100.0
+            d = -C[m] * (v @ G @ v) * 1e-12 / tot[m] ** 2 / (self.nq * P.crystal.volume * 1e-30)
+            for ch in range(5):
+                if channel_mask >> ch & 1:
+                    out[ch, m] = d
+        return torch.from_numpy(out)
+
+    def backward(self, dg):
+        g3, g4 = self.P.grad(self._modes, dg.numpy(), self._mask)
+        return torch.from_numpy(g3), torch.from_numpy(g4)
+
+
+def _worker_grad(rank, world, port, out_dir):
+    import oracle
+    from synth import morse_system
+    from paper_2510_00518_gb300.dist import sharded_kappa_gradient
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    if world > 1:
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        eng = _OracleGradEngine(oracle.Problem(*morse_system(seed=0), (3, 2, 2)))
+        dk = np.array([[1.0, 0.2, 0.0], [0.2, -0.5, 0.1], [0.0, 0.1, 0.3]])
+        k, d3, d4 = sharded_kappa_gradient(eng, 300.0, 0.1, dk, channel_mask=0b11)
+        np.save(os.path.join(out_dir, f"g{world}_{rank}.npy"), np.concatenate([k.numpy().reshape(-1), d3.numpy().reshape(-1)]))
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+def test_two_rank_gradient_allreduce(tmp_path):
+    """dL/dΦ3 of L = Σ G κ with the modes split over two ranks (rates, κ all-reduce, adjoint of each
+    rank's own modes, one gradient all-reduce) equals the single-rank result."""
+    _worker_grad(0, 1, _free_port(), str(tmp_path))
+    mp.start_processes(_worker_grad, args=(2, _free_port(), str(tmp_path)), nprocs=2,
+                       start_method="spawn", join=True)
+    ref = np.load(tmp_path / "g1_0.npy")
+    assert np.abs(ref[9:]).max() > 0
+    for r in range(2):
+        x = np.load(tmp_path / f"g2_{r}.npy")
+        assert np.allclose(x, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())

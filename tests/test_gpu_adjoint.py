@@ -20,11 +20,11 @@ def sysm():
     return morse_system(seed=0)
 
 
-def test_rates_backward_matches_oracle_gradient(sysm):
-    mesh = (3, 3, 3)
+@pytest.mark.parametrize("mesh,sub", [((3, 3, 3), [13]), ((4, 4, 4), [22])])
+def test_rates_backward_matches_oracle_gradient(sysm, mesh, sub):
+    """3x3x3, and the 4x4x4 mesh of the differentiation workload's oracle comparison."""
     prob = oracle.Problem(*sysm, mesh)
     e = make_engine(sysm, mesh, precision=0, prob=prob)
-    sub = [13]
     modes = modes_of(sub, 6)
     rng = np.random.default_rng(2)
     dL = rng.standard_normal((5, modes.size))
@@ -34,6 +34,27 @@ def test_rates_backward_matches_oracle_gradient(sysm):
     # different FP64 summation orders over sums with cancellation: 1e-8 relative, floor 1e-9 max
     assert_close(d3.cpu().numpy().reshape(-1), g3.reshape(-1), 1e-8, floor_frac=1e-9, what="dphi3")
     assert_close(d4.cpu().numpy().reshape(-1), g4.reshape(-1), 1e-8, floor_frac=1e-9, what="dphi4")
+
+
+def test_rates_backward_four_atom_cell():
+    """A 4-atom cell with random clusters on up to four distinct sites (no pair structure)."""
+    from synth import diamond_crystal, supercell_crystal, morse_ifcs, random_cluster_ifcs
+    c = supercell_crystal(diamond_crystal(), 2, masses=np.array([28.0855, 12.0, 72.6, 28.0855]))
+    p2, _, _ = morse_ifcs(c, seed=3)
+    p3 = random_cluster_ifcs(c, 3, 40, seed=4, scale=2.0)
+    p4 = random_cluster_ifcs(c, 4, 60, seed=5, scale=5.0)
+    sys4 = (c, p2, p3, p4)
+    mesh = (2, 2, 2)
+    prob = oracle.Problem(*sys4, mesh)
+    e = make_engine(sys4, mesh, precision=0, prob=prob)
+    sub = [3]
+    modes = modes_of(sub, 12)
+    dL = np.random.default_rng(7).standard_normal((5, modes.size))
+    e.rates(300.0, 0.1, 31, q_subset=sub)
+    d3, d4 = e.backward(torch.tensor(dL, device="cuda"))
+    g3, g4 = prob.grad(modes, dL)
+    assert_close(d3.cpu().numpy().reshape(-1), g3.reshape(-1), 1e-8, floor_frac=1e-9, what="dphi3 (4 atoms)")
+    assert_close(d4.cpu().numpy().reshape(-1), g4.reshape(-1), 1e-8, floor_frac=1e-9, what="dphi4 (4 atoms)")
 
 
 def test_rates_backward_deterministic_and_euler(sysm):

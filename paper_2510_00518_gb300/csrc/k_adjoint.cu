@@ -256,35 +256,34 @@ adj3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
     const int4 c0 = t.qc[q0];
     const double w0 = t.om[m0];
     __syncthreads();
-    for (int qb = 0; qb < N; qb += kAdjThreads) {
+    for (int qb = 0; qb < N; qb += kAdjThreads)
+      for (int j1 = 0; j1 < NB; ++j1) {           // one partner branch j' at a time (NB <= 24 bits)
         const int q1 = qb + threadIdx.x;
-        // this thread's kept processes (j', j'') at q', in order
-        unsigned long long kept = 0;
+        // this thread's kept processes (j'', ascending) at (q', j')
+        unsigned kept = 0;
         int q2 = 0;
         if (q1 < N) {
             const int4 c1 = t.qc[q1];
             q2 = q_index(c0.x + s * c1.x, c0.y + s * c1.y, c0.z + s * c1.z, t.mesh[0], t.mesh[1], t.mesh[2]);
             const unsigned v1 = t.vmask[q1], v2 = t.vmask[q2];
-            for (int j1 = 0; j1 < NB; ++j1)
-                for (int j2 = 0; j2 < NB; ++j2)
-                    if (((v1 >> j1) & (v2 >> j2) & 1u) &&
-                        (a.adaptive ? window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2, -1,
-                                                            q1 * NB + j1, q2 * NB + j2)
-                                    : fabs(delta_exact(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], 0.0)) <= a.two_sigma))
-                        kept |= 1ull << (j1 * NB + j2);
+            for (int j2 = 0; j2 < NB; ++j2)
+                if (((v1 >> j1) & (v2 >> j2) & 1u) &&
+                    (a.adaptive ? window_exact_adaptive(t, a, ch, m0, q1 * NB + j1, q2 * NB + j2, -1,
+                                                        q1 * NB + j1, q2 * NB + j2)
+                                : fabs(delta_exact(ch, w0, t.om[q1 * NB + j1], t.om[q2 * NB + j2], 0.0)) <= a.two_sigma))
+                    kept |= 1u << j2;
         }
         if (threadIdx.x == 0) s_max = 0;
         __syncthreads();
-        atomicMax(&s_max, __popcll(kept));
+        atomicMax(&s_max, __popc(kept));
         __syncthreads();
         const int rounds = s_max;
         for (int sr = 0; sr < rounds; ++sr) {
             Item3 it;
             const bool has = kept != 0;
             if (has) {
-                const int k = __ffsll(kept) - 1;
+                const int j2 = __ffs(kept) - 1;
                 kept &= kept - 1;
-                const int j1 = k / NB, j2 = k - j1 * NB;
                 const int m1 = q1 * NB + j1, m2 = q2 * NB + j2;
                 const int4 c1 = t.qc[q1];
                 C V = czero<C>();

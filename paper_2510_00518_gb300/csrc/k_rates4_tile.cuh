@@ -246,6 +246,17 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     }
                     const unsigned long long tri_bits = (unsigned long long)tri << 36;
                     if constexpr (ADA) {
+                        if (ch != 3) {   // ++, --: most (q'', j') have no pair near its window at all
+                            float mn = 1.0f;
+#pragma unroll
+                            for (int j3 = 0; j3 < NB; ++j3)
+#pragma unroll
+                                for (int j2 = 0; j2 < NB; ++j2) {
+                                    const float g = s_g[(j3 * NB + j2) * kTileQ + threadIdx.x];
+                                    mn = fminf(mn, fabsf((b + w2f[j2]) - w3f[j3]) - fmaf(a.ad_rhi, g, a.ad_e0));
+                                }
+                            if (!(mn <= 0.0f)) continue;         // nothing kept, nothing ambiguous
+                        }
                         unsigned long long sure = 0, amb = 0;
 #pragma unroll
                         for (int j3 = 0; j3 < NB; ++j3)

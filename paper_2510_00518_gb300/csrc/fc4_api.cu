@@ -70,6 +70,8 @@ struct fc4_ctx {
     double2 *ev = nullptr;
     float2 *ev32 = nullptr;
     float4 *vp32 = nullptr, *vp32lo = nullptr;
+    float *omT32 = nullptr;                 // branch-major window copies [nb][N]
+    float4 *vpT32 = nullptr, *vpTlo = nullptr;
     unsigned *vmask = nullptr;
     int *err = nullptr;
     double occ_T = -1.0;
@@ -181,7 +183,7 @@ fc4_status check_ifc(const fc4_ifc *f, int order, int n_atoms, bool required, co
 // Rebuild the derived mode tables after ω / e changed (also zeroes the excluded ω).
 fc4_status refresh_modes(fc4_ctx *c) {
     FC4_CUDA(c, fc4::launch_mode_tables(c->t, c->om, c->om32, c->om32lo, c->ev32, c->ev, c->vmask,
-                                        c->invw, c->invw32, c->vp32, c->vp32lo, 0));
+                                        c->invw, c->invw32, c->vp32, c->vp32lo, c->omT32, c->vpT32, c->vpTlo, 0));
     const size_t nm = (size_t)c->t.N * c->t.nb;
     c->om_host.assign(nm, 0.0);
     FC4_CUDA(c, cudaMemcpy(c->om_host.data(), c->om, nm * sizeof(double), cudaMemcpyDeviceToHost));
@@ -624,6 +626,9 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     FC4_TRY(dalloc(c, &c->vmask, (size_t)N));
     FC4_TRY(dalloc(c, &c->vp32, nm));
     FC4_TRY(dalloc(c, &c->vp32lo, nm));
+    FC4_TRY(dalloc(c, &c->omT32, nm));
+    FC4_TRY(dalloc(c, &c->vpT32, nm));
+    FC4_TRY(dalloc(c, &c->vpTlo, nm));
     FC4_TRY(dalloc(c, &c->err, 1));
     FC4_TRY(cudaMemset(c->err, 0, sizeof(int)));
     FC4_TRY(dalloc(c, &c->dev_err, 1));
@@ -637,6 +642,9 @@ fc4_status fc4_init(const fc4_crystal *crystal, const fc4_ifc *phi2, const fc4_i
     t.vmask = c->vmask;
     t.vp32 = c->vp32;
     t.vp32lo = c->vp32lo;
+    t.omT32 = c->omT32;
+    t.vpT32 = c->vpT32;
+    t.vpTlo = c->vpTlo;
     t.occ = c->occ;
     t.occ32 = c->occ32;
     t.invw = c->invw;

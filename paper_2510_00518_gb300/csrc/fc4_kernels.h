@@ -29,6 +29,10 @@ struct Tables {
     const unsigned *vmask;       // [N] bit j set iff mode (q, j) takes part
     const float4 *vp32;          // [N*nb] P_k = (v . b_k) / n_k, k = 1..3 (rad/ps), FP32 hi parts
     const float4 *vp32lo;        // [N*nb] P_k - hi, FP32 (lo parts)
+    // branch-major copies for the window, whose lanes read consecutive q: [nb][N]
+    const float *omT32;          // ω hi
+    const float4 *vpT32;         // P hi
+    const float4 *vpTlo;         // P lo
     double recip[9];             // reciprocal vectors b_k (rows, 1/Å), a_i . b_k = 2π δ_ik
     // occupations at the current T
     const double *occ;           // [N*nb]
@@ -137,7 +141,8 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
                             int *err, cudaStream_t s);
 cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
                                float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
-                               float *invw32, float4 *vp32, float4 *vp32lo, cudaStream_t s);
+                               float *invw32, float4 *vp32, float4 *vp32lo, float *omT32, float4 *vpT32,
+                               float4 *vpTlo, cudaStream_t s);
 cudaError_t launch_occupations(const Tables &t, double hbar_over_kT, double *occ, float *occ32,
                                cudaStream_t s);
 // message returned by fc4_last_error(NULL) (errors of calls without a context)

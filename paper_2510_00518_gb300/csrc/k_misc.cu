@@ -178,7 +178,8 @@ cudaError_t launch_harmonic(const Tables &t, int nc2, const int4 *c2_at, const i
 // adaptive width.
 __global__ void mode_tables_kernel(const __grid_constant__ Tables t, double *om, float *om32, float *om32lo,
                                    float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
-                                   float *invw32, float4 *vp32, float4 *vp32lo) {
+                                   float *invw32, float4 *vp32, float4 *vp32lo, float *omT32, float4 *vpT32,
+                                   float4 *vpTlo) {
     const int N = t.N, nb = t.nb;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nm = (long long)N * nb;
@@ -200,6 +201,10 @@ __global__ void mode_tables_kernel(const __grid_constant__ Tables t, double *om,
         }
         vp32[i] = make_float4(h[0], h[1], h[2], 0.0f);
         vp32lo[i] = make_float4(l[0], l[1], l[2], 0.0f);
+        const size_t it = (size_t)j * N + q;                 // branch-major copies
+        omT32[it] = (float)w;
+        vpT32[it] = make_float4(h[0], h[1], h[2], 0.0f);
+        vpTlo[it] = make_float4(l[0], l[1], l[2], 0.0f);
     }
     if (i < nm * nb) {
         const double2 e = ev[i];
@@ -215,10 +220,11 @@ __global__ void mode_tables_kernel(const __grid_constant__ Tables t, double *om,
 
 cudaError_t launch_mode_tables(const Tables &t, double *om, float *om32, float *om32lo,
                                float2 *ev32, const double2 *ev, unsigned *vmask, double *invw,
-                               float *invw32, float4 *vp32, float4 *vp32lo, cudaStream_t s) {
+                               float *invw32, float4 *vp32, float4 *vp32lo, float *omT32, float4 *vpT32,
+                               float4 *vpTlo, cudaStream_t s) {
     const long long n = (long long)t.N * t.nb * t.nb;
     mode_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, om, om32, om32lo, ev32, ev, vmask, invw,
-                                                                    invw32, vp32, vp32lo);
+                                                                    invw32, vp32, vp32lo, omT32, vpT32, vpTlo);
     return cudaGetLastError();
 }
 

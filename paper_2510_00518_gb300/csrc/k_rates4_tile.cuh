@@ -196,8 +196,8 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 float w2f[NB], w3f[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
-                    w2f[j] = (float)s2 * t.om32[q2 * NB + j];
-                    w3f[j] = t.om32[q3 * NB + j];
+                    w2f[j] = (float)s2 * t.omT32[j * N + q2];   // branch-major: lanes read consecutive q
+                    w3f[j] = t.omT32[j * N + q3];
                 }
                 // Triangular domain (partner-swap symmetry of the summand): +- is symmetric under
                 // (λ'', λ''') (q'' <-> q''' at fixed q'), ++ and -- under (λ', λ'') (q' <-> q'') when σ
@@ -224,12 +224,11 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                 if constexpr (ADA) {
 #pragma unroll 1
                     for (int j3 = 0; j3 < NB; ++j3) {
-                        const int m3 = q3 * NB + j3;
-                        const float4 h3 = t.vp32[m3], l3 = t.vp32lo[m3];
+                        const float4 h3 = t.vpT32[j3 * N + q3], l3 = t.vpTlo[j3 * N + q3];
 #pragma unroll
                         for (int j2 = 0; j2 < NB; ++j2)
                             s_g[(j3 * NB + j2) * kTileQ + threadIdx.x] =
-                                a.ad_c32 * vel_diff_norm32(t.vp32[q2 * NB + j2], t.vp32lo[q2 * NB + j2], h3, l3);
+                                a.ad_c32 * vel_diff_norm32(t.vpT32[j2 * N + q2], t.vpTlo[j2 * N + q2], h3, l3);
                     }
                 }
 #pragma unroll 1

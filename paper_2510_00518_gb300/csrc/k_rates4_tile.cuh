@@ -15,9 +15,18 @@
 namespace fc4 {
 
 constexpr int kTileQ = 128;
-// partner points q'' per thread and compaction round: 4 for the sparse ++ and -- channels (more
-// window work per round), 2 for +- (fewer registers held across its dense entry work)
+// Partner points q'' per thread and compaction round, and blocks per SM.  Fixed σ: 4 for the
+// sparse ++ and -- channels (more window work per round), 2 for +- (fewer registers held across
+// its dense entry work), 4 blocks of 128 threads per SM (128 registers).  Adaptive σ carries the
+// pair widths and the per-process width through the same loops: at 128 registers it spilled
+// (~500 bytes), so it runs 3 blocks per SM (168 registers) with 2 and 1 q'' per round; measured on
+// the 16^3 precision workload this took a 5-q batch from 792 to 614 ms, while the fixed-σ kernels
+// lose 1-3 % with either change.
 constexpr int kQPTSparse = 4, kQPTDense = 2;
+constexpr int kQPTSparseAd = 2, kQPTDenseAd = 1;
+template <bool ADA> constexpr int qpt_of(bool dense) {
+    return ADA ? (dense ? kQPTDenseAd : kQPTSparseAd) : (dense ? kQPTDense : kQPTSparse);
+}
 // q'' per chunk of the +- triangle list (the q'' <= q''' of a unit, built in shared memory)
 constexpr int kTriChunk = 1024;
 
@@ -109,7 +118,7 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
 //   Δ_λ = Σ_p γ_p Σ_k s_k (ω_k / ω_λ) F_k  (partner signs: ++ (-, -, +), +- (-, +, +), -- (+, +, +)),
 // into a.part_d; the partner combination is symmetric under the swap the triangular domain uses.
 template <typename R, int NA, bool ADA, int kQPT, bool BTE = false>
-__global__ void __launch_bounds__(kTileQ, 4)
+__global__ void __launch_bounds__(kTileQ, ADA ? 3 : 4)
 rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
                    int mode0, const Cplx<R> *__restrict__ wall) {
     using C = Cplx<R>;
@@ -512,8 +521,9 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
     using C = Cplx<R>;
     constexpr int NB = 3 * NA;
     const bool dense = ch == 3;
-    const size_t smem = tile_smem_bytes<R, NA>(t, dense ? kQPTDense : kQPTSparse, ADA);
-    auto kern = dense ? rates4_tile_kernel<R, NA, ADA, kQPTDense, BTE> : rates4_tile_kernel<R, NA, ADA, kQPTSparse, BTE>;
+    const size_t smem = tile_smem_bytes<R, NA>(t, qpt_of<ADA>(dense), ADA);
+    auto kern = dense ? rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(true), BTE>
+                      : rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(false), BTE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB + (size_t)t.n_keys * NA * 27);

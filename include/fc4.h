@@ -381,6 +381,36 @@ fc4_status fc4_irreducible_q(const int mesh[3], int n_ops, const int *rot, int f
 fc4_status fc4_expand_irreducible(const int mesh[3], int nb, const int *rep, const double *omega,
                                   double deg_tol, int n_sets, const double *sub, double *full);
 
+/* ---------------------------------------------------------------- batches of crystals
+ * Many contexts (crystals of different cell sizes, meshes and clusters) evaluated together.
+ * fc4_batch_rates runs the four-phonon units (λ, q') of every context with the same cell size as
+ * ONE persistent launch of the general kernel: a work list of (context, channel, unit) from the
+ * largest meshes down, each 128-thread block taking the next item from a global counter, so that
+ * the uneven per-crystal and per-q work balances across the whole GPU; three-phonon kernels and
+ * reductions run per context.  FP32 contractions (contexts of any precision but FC4_FP64), fixed
+ * σ, no tensor cores; Γ, WP and counts equal those of fc4_rates_static on each context (the same
+ * kernel arithmetic).  After a first call with the same arguments (which sizes every buffer), a
+ * call performs only stream-ordered launches and memsets, so it can be captured in a CUDA graph. */
+
+typedef struct fc4_batch fc4_batch;
+
+/* fc4_batch_create - a batch over n contexts (the contexts must outlive it; not copied). */
+fc4_status fc4_batch_create(fc4_ctx *const *ctxs, int n, fc4_batch **out);
+
+/* fc4_batch_rates - rates of every context: q_subsets[i] (host, n_q[i] q points; q_subsets or
+ * q_subsets[i] NULL = all q), fixed σ sigma_value THz, T_K > 0, channel_mask as for fc4_rates;
+ * gamma_out[i] (and wp_out[i], counts_out[i] if the arrays are not NULL): device [5][n_q nb] of
+ * context i.  fc4_stats of each context reports its part. */
+fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_value, int channel_mask,
+                           const int *const *q_subsets, const int *n_q, double *const *gamma_out,
+                           double *const *wp_out, long long *const *counts_out, void *stream);
+
+/* fc4_batch_last_error - message of the last failed call on b. */
+const char *fc4_batch_last_error(const fc4_batch *b);
+
+/* fc4_batch_destroy - free the batch (not its contexts; NULL is a no-op). */
+void fc4_batch_destroy(fc4_batch *b);
+
 /* fc4_device_peaks - calibration of the current device's CUDA cores (no context): out[0] the FP32
  * and out[1] the FP64 fused multiply-add rate in TFLOP/s (2 flops per FMA), each timed with CUDA
  * events on `stream` over one launch of 8 x 256-thread blocks per SM running 8 independent FMA

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["FC4Error", "load", "Engine", "FP64", "MIXED", "TF32X3", "BF16", "BF16X3", "FP16X3",
+__all__ = ["FC4Error", "load", "Engine", "Batch", "FP64", "MIXED", "TF32X3", "BF16", "BF16X3", "FP16X3",
            "PRECISIONS", "CHANNELS", "lib_path", "rates_fn", "kappa_fn"]
 
 # fc4_precision: FP64; FP32 on the CUDA cores; and the tensor-core operand formats of the 4ph +-
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = False):
         "fc4_set_mode_chunk": [vp, i, ll],
         "fc4_memory": [vp, vp],
         "fc4_device_peaks": [vp, vp],
+        "fc4_batch_create": [vp, i, vp],
+        "fc4_batch_rates": [vp, d, d, i, vp, vp, vp, vp, vp, vp],
         "fc4_check_device": [vp],
         "fc4_symmetry_ops": [ctypes.POINTER(_Crystal), ctypes.POINTER(_IFC), ctypes.POINTER(_IFC),
                              ctypes.POINTER(_IFC), d, i, vp, vp, vp],
@@ -106,6 +108,10 @@ def load(build_if_missing: bool = False):
     lib.fc4_last_error.restype = ctypes.c_char_p
     lib.fc4_destroy.argtypes = [vp]
     lib.fc4_destroy.restype = None
+    lib.fc4_batch_last_error.argtypes = [vp]
+    lib.fc4_batch_last_error.restype = ctypes.c_char_p
+    lib.fc4_batch_destroy.argtypes = [vp]
+    lib.fc4_batch_destroy.restype = None
     _LIB = lib
     return lib
 
@@ -409,6 +415,59 @@ class Engine:
         p4 = None if phi4 is None else _np(phi4, np.float64)
         self._check(self.lib.fc4_update_anharmonic(self.ctx, None if p3 is None else _ptr(p3),
                                                    None if p4 is None else _ptr(p4)))
+
+
+class Batch:
+    """Rates of many engines together (fc4_batch_rates): the four-phonon units of all engines with
+    the same cell size run as one persistent launch over a shared work list."""
+
+    def __init__(self, engines):
+        self.lib = load()
+        self.engines = list(engines)
+        arr = (ctypes.c_void_p * len(self.engines))(*[e.ctx.value for e in self.engines])
+        b = ctypes.c_void_p()
+        st = self.lib.fc4_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.engines), ctypes.byref(b))
+        if st != 0:
+            raise FC4Error(st, self.lib.fc4_last_error(None).decode())
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fc4_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self, T: float, sigma_thz: float, channel_mask: int = 31, q_subsets=None, outs=None, stream=None):
+        """[(Γ, WP, counts)] per engine, each [5, n_q nb] CUDA tensors (fixed σ in THz)."""
+        import torch
+        n = len(self.engines)
+        qs = [None if q_subsets is None or q_subsets[i] is None else _np(q_subsets[i], np.int32) for i in range(n)]
+        if outs is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            outs = []
+            for e, q in zip(self.engines, qs):
+                nm = (e.nq if q is None else q.size) * e.nb
+                outs.append((torch.empty((5, nm), dtype=torch.float64, device=dev),
+                             torch.empty((5, nm), dtype=torch.float64, device=dev),
+                             torch.empty((5, nm), dtype=torch.int64, device=dev)))
+        self._keep = qs                              # host q lists must outlive the call
+        qp = (ctypes.c_void_p * n)(*[None if q is None else q.ctypes.data for q in qs])
+        nq = (ctypes.c_int * n)(*[0 if q is None else q.size for q in qs])
+        gp = (ctypes.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+        wp = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in outs])
+        cp = (ctypes.c_void_p * n)(*[o[2].data_ptr() for o in outs])
+        st = self.lib.fc4_batch_rates(self.b, float(T), float(sigma_thz), int(channel_mask),
+                                      ctypes.cast(qp, ctypes.c_void_p), ctypes.cast(nq, ctypes.c_void_p),
+                                      ctypes.cast(gp, ctypes.c_void_p), ctypes.cast(wp, ctypes.c_void_p),
+                                      ctypes.cast(cp, ctypes.c_void_p), _stream(stream))
+        if st != 0:
+            raise FC4Error(st, self.lib.fc4_batch_last_error(self.b).decode())
+        return outs
 
 
 # ------------------------------------------------------------------------------ autograd

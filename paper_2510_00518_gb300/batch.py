@@ -1,9 +1,12 @@
 """Many crystals in one CUDA-graph launch, with a small autotuner.
 
 Each crystal is its own fc4 context (its own cell size, mesh and clusters).  ``BatchRunner``
-runs every context's ``fc4_rates`` once eagerly (which sizes every buffer), then captures all
-of them, in order, on one stream into one CUDA graph; ``run()`` replays it with a single
-launch.  ``autotune`` picks the general four-phonon kernel's block size per context by timing
+runs the batch once eagerly (which sizes every buffer), then captures it on one stream into one
+CUDA graph; ``run()`` replays it with a single launch.  ``persistent=True`` (the default) captures
+one ``fc4_batch_rates`` call: the four-phonon units of all crystals of the same cell size run as one
+persistent launch over a shared work list (largest meshes first), so uneven per-crystal work
+balances over the whole GPU.  ``persistent=False`` captures every context's ``fc4_rates`` in turn
+(the tiled kernels for cells of up to two atoms).  ``autotune`` picks the general four-phonon kernel's block size per context by timing
 the candidates with CUDA events, and caches the choice in a JSON file keyed by the context's
 shape (atoms, mesh, precision, subset size)."""
 from __future__ import annotations
@@ -56,21 +59,29 @@ def autotune(engine, T: float, sigma_thz: float, channel_mask: int, q_subset, ca
 class BatchRunner:
     """Rates of many contexts as one CUDA graph (one launch per ``run``)."""
 
-    def __init__(self, jobs, T: float, sigma_thz: float, channel_mask: int = 31):
+    def __init__(self, jobs, T: float, sigma_thz: float, channel_mask: int = 31, persistent: bool = True):
         """jobs: list of (engine, q_subset or None)."""
         import torch
+        from . import Batch
         self.jobs = jobs
         self.T, self.sigma, self.mask = T, sigma_thz, channel_mask
         self.stream = torch.cuda.Stream()
-        self.outs = []
-        with torch.cuda.stream(self.stream):
-            for eng, qs in jobs:                        # eager pass: sizes all buffers
-                self.outs.append(eng.rates(T, sigma_thz, channel_mask, q_subset=qs, stream=self.stream))
+        self.batch = Batch([e for e, _ in jobs]) if persistent else None
+        qsets = [qs for _, qs in jobs]
+        with torch.cuda.stream(self.stream):           # eager pass: sizes all buffers
+            if self.batch is not None:
+                self.outs = self.batch.rates(T, sigma_thz, channel_mask, q_subsets=qsets, stream=self.stream)
+            else:
+                self.outs = [eng.rates(T, sigma_thz, channel_mask, q_subset=qs, stream=self.stream)
+                             for eng, qs in jobs]
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
-            for (eng, qs), out in zip(jobs, self.outs):
-                eng.rates(T, sigma_thz, channel_mask, q_subset=qs, out=out, stream=self.stream)
+            if self.batch is not None:
+                self.batch.rates(T, sigma_thz, channel_mask, q_subsets=qsets, outs=self.outs, stream=self.stream)
+            else:
+                for (eng, qs), out in zip(jobs, self.outs):
+                    eng.rates(T, sigma_thz, channel_mask, q_subset=qs, out=out, stream=self.stream)
 
     def run(self):
         self.graph.replay()

@@ -1336,3 +1336,232 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
                                    counts_out, nullptr, s));
     return FC4_OK;
 }
+
+// ------------------------------------------------------------------------------ batched contexts
+//
+// fc4_batch_rates: the rates of many contexts in a few launches.  The four-phonon units of every
+// context with the same cell size run as one persistent launch of the general kernel (FP32, fixed
+// σ) over a work list (context, channel, unit) ordered from the largest meshes down, each block
+// taking the next item from a global counter; the three-phonon kernels and the reductions are
+// launched per context.  With unchanged arguments a call performs only stream-ordered launches and
+// memsets (no host copies), so it can be captured in a CUDA graph.
+
+struct fc4_batch {
+    std::vector<fc4_ctx *> ctx;
+    fc4::Tables *d_tabs = nullptr;
+    fc4::RateArgs *d_args = nullptr;
+    std::vector<fc4::RateArgs> args_on_device;
+    int4 *d_items = nullptr;
+    size_t items_cap = 0;
+    std::vector<int4> items_on_device;
+    int *d_counter = nullptr;                  // one counter per cell size (1..8 atoms)
+    std::string last_error;
+};
+
+namespace {
+
+fc4_status bfail(fc4_batch *b, fc4_status s, const std::string &msg) {
+    if (b) b->last_error = msg;
+    else fc4::set_host_error(msg.c_str());
+    return s;
+}
+
+#define FC4_BCUDA(b, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? FC4_ERR_OOM : FC4_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+fc4_status fc4_batch_create(fc4_ctx *const *ctxs, int n, fc4_batch **out) {
+    if (!out || !ctxs || n <= 0) return bfail(nullptr, FC4_ERR_INVALID, "fc4_batch_create: ctxs, n > 0 and out required");
+    *out = nullptr;
+    fc4_batch *b = new fc4_batch();
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) { delete b; return bfail(nullptr, FC4_ERR_INVALID, "fc4_batch_create: NULL context"); }
+        b->ctx.push_back(ctxs[i]);
+    }
+    std::vector<fc4::Tables> tabs;
+    for (fc4_ctx *c : b->ctx) tabs.push_back(c->t);
+    cudaError_t e = cudaMalloc((void **)&b->d_tabs, sizeof(fc4::Tables) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, sizeof(fc4::RateArgs) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, sizeof(int) * 9);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tabs, tabs.data(), sizeof(fc4::Tables) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fc4_batch_destroy(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? FC4_ERR_OOM : FC4_ERR_CUDA,
+                     std::string("fc4_batch_create: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return FC4_OK;
+}
+
+const char *fc4_batch_last_error(const fc4_batch *b) { return b ? b->last_error.c_str() : ""; }
+
+void fc4_batch_destroy(fc4_batch *b) {
+    if (!b) return;
+    cudaFree(b->d_tabs);
+    cudaFree(b->d_args);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    delete b;
+}
+
+}  // extern "C"
+
+extern "C" fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_value, int channel_mask,
+                                      const int *const *q_subsets, const int *n_q, double *const *gamma_out,
+                                      double *const *wp_out, long long *const *counts_out, void *stream) {
+    if (!b) return bfail(nullptr, FC4_ERR_INVALID, "batch is NULL");
+    if (!(T_K > 0.0) || !std::isfinite(T_K)) return bfail(b, FC4_ERR_INVALID, "T must be > 0");
+    if (!(sigma_value > 0.0) || !std::isfinite(sigma_value)) return bfail(b, FC4_ERR_INVALID, "sigma must be > 0");
+    if (channel_mask < 0 || channel_mask > 31) return bfail(b, FC4_ERR_INVALID, "channel_mask must be in [0, 31]");
+    if (!gamma_out) return bfail(b, FC4_ERR_INVALID, "gamma_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)b->ctx.size();
+    std::vector<fc4::RateArgs> args(n);
+    std::vector<int> nms(n);
+    for (int i = 0; i < n; ++i) {
+        fc4_ctx *c = b->ctx[i];
+        if (c->precision == FC4_FP64) return bfail(b, FC4_ERR_INVALID, "fc4_batch_rates: FP32 contexts only");
+        const int N = c->t.N, nb = c->t.nb;
+        std::vector<int> modes;
+        if (q_subsets && q_subsets[i]) {
+            if (!n_q || n_q[i] < 0) return bfail(b, FC4_ERR_INVALID, "n_q required with q_subsets");
+            for (int k = 0; k < n_q[i]; ++k) {
+                const int q = q_subsets[i][k];
+                if (q < 0 || q >= N) return bfail(b, FC4_ERR_INVALID, "q index out of range");
+                for (int j = 0; j < nb; ++j) modes.push_back(q * nb + j);
+            }
+        } else {
+            modes.resize((size_t)N * nb);
+            std::iota(modes.begin(), modes.end(), 0);
+        }
+        const int nm = (int)modes.size();
+        nms[i] = nm;
+        if (nm == 0) continue;
+        if (!gamma_out[i]) return bfail(b, FC4_ERR_INVALID, "gamma_out[i] is NULL");
+        if ((size_t)nm > c->modes_cap) {
+            if (c->modes) { cudaFree(c->modes); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void *)c->modes)); }
+            c->modes = nullptr;
+            c->modes_cap = 0;
+            FC4_BCUDA(b, dalloc(c, &c->modes, (size_t)nm));
+            c->modes_cap = nm;
+            c->modes_on_device.clear();
+        }
+        const size_t need = (size_t)5 * nm * N;
+        if (need > c->part_cap) {
+            for (void *p : {(void *)c->part_g, (void *)c->part_wp, (void *)c->part_n, (void *)c->part_items,
+                            (void *)c->part_ent, (void *)c->part_ev, (void *)c->part_cev})
+                if (p) { cudaFree(p); c->owned.erase(std::find(c->owned.begin(), c->owned.end(), p)); }
+            c->part_g = c->part_wp = nullptr;
+            c->part_n = c->part_items = c->part_ent = c->part_ev = c->part_cev = nullptr;
+            c->part_cap = 0;
+            FC4_BCUDA(b, dalloc(c, &c->part_g, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_wp, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_n, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_items, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_ent, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_ev, need));
+            FC4_BCUDA(b, dalloc(c, &c->part_cev, need));
+            c->part_cap = need;
+        }
+        if (modes != c->modes_on_device) {
+            FC4_BCUDA(b, cudaMemcpyAsync(c->modes, modes.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+            c->modes_on_device = modes;
+        }
+        if (ensure_occupations(c, T_K, s) != FC4_OK) return bfail(b, FC4_ERR_CUDA, c->last_error);
+        if (!c->stats) FC4_BCUDA(b, dalloc(c, &c->stats, 25));
+        FC4_BCUDA(b, cudaMemsetAsync(c->stats, 0, 25 * sizeof(unsigned long long), s));
+        fc4::RateArgs &a = args[i];
+        a.n_modes = nm;
+        a.modes = c->modes;
+        set_window(c, a, false, sigma_value);
+        a.use_tc = 0;
+        a.part_g = c->part_g;
+        a.part_wp = c->part_wp;
+        a.part_n = c->part_n;
+        a.part_items = c->part_items;
+        a.part_ent = c->part_ent;
+        a.part_ev = c->part_ev;
+        a.part_cev = c->part_cev;
+        for (int ch = 2; ch < 5; ++ch)
+            if (((channel_mask >> ch) & 1) && c->nc4) a.n_part[ch] = N;
+        c->cand[0] = c->cand[1] = c->cand[2] = c->cand[3] = c->cand[4] = 0;
+        for (int ch = 0; ch < 5; ++ch)
+            if ((channel_mask >> ch) & 1)
+                c->cand[ch] = (ch < 2 ? (long long)N * nb * nb : (long long)N * N * nb * nb * nb) * nm;
+    }
+    // three-phonon kernels per context (they set n_part of their channels)
+    for (int i = 0; i < n; ++i) {
+        fc4_ctx *c = b->ctx[i];
+        if (!nms[i] || !c->nc3) continue;
+        for (int ch = 0; ch < 2; ++ch)
+            if ((channel_mask >> ch) & 1) FC4_BCUDA(b, fc4::launch_rates3(c->t, args[i], ch, 0, s));
+    }
+    // work list: contexts grouped by cell size (largest first), meshes from the largest down
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const fc4::Tables &tx = b->ctx[x]->t, &ty = b->ctx[y]->t;
+        return tx.n_atoms != ty.n_atoms ? tx.n_atoms > ty.n_atoms : tx.N > ty.N;
+    });
+    std::vector<int4> items;
+    std::vector<std::array<long long, 3>> classes;      // (atoms, first item, count)
+    for (int i : order) {
+        fc4_ctx *c = b->ctx[i];
+        if (!nms[i] || !c->nc4) continue;
+        if (classes.empty() || classes.back()[0] != c->t.n_atoms)
+            classes.push_back({(long long)c->t.n_atoms, (long long)items.size(), 0});
+        const long long units = (long long)nms[i] * c->t.N;
+        for (int ch = 2; ch < 5; ++ch) {
+            if (!((channel_mask >> ch) & 1)) continue;
+            for (long long u = 0; u < units; ++u) items.push_back(make_int4(i, ch, (int)u, 0));
+        }
+        classes.back()[2] = (long long)items.size() - classes.back()[1];
+    }
+    if (items.size() > 0x7fffffffULL) return bfail(b, FC4_ERR_INVALID, "fc4_batch_rates: too many units");
+    if (args.size() != b->args_on_device.size() ||
+        std::memcmp(args.data(), b->args_on_device.data(), sizeof(fc4::RateArgs) * args.size()) != 0) {
+        FC4_BCUDA(b, cudaMemcpyAsync(b->d_args, args.data(), sizeof(fc4::RateArgs) * n, cudaMemcpyHostToDevice, s));
+        b->args_on_device = args;
+    }
+    if (items.size() != b->items_on_device.size() ||
+        std::memcmp(items.data(), b->items_on_device.data(), sizeof(int4) * items.size()) != 0) {
+        if (items.size() > b->items_cap) {
+            cudaFree(b->d_items);
+            b->d_items = nullptr;
+            b->items_cap = 0;
+            FC4_BCUDA(b, cudaMalloc((void **)&b->d_items, sizeof(int4) * items.size()));
+            b->items_cap = items.size();
+        }
+        if (!items.empty())
+            FC4_BCUDA(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+        b->items_on_device = items;
+    }
+    for (size_t k = 0; k < classes.size(); ++k) {
+        const int na = (int)classes[k][0];
+        size_t smem = 0;
+        for (int i : order)
+            if (b->ctx[i]->t.n_atoms == na) smem = std::max(smem, fc4::general_smem_f(na, b->ctx[i]->t));
+        FC4_BCUDA(b, cudaMemsetAsync(b->d_counter + na, 0, sizeof(int), s));
+        const int4 *it = b->d_items + classes[k][1];
+        const int cnt = (int)classes[k][2];
+        FC4_BCUDA(b, na <= 4 ? fc4::launch4_batch_f_1_4(na, b->d_tabs, b->d_args, it, cnt, b->d_counter + na, smem, s)
+                             : fc4::launch4_batch_f_5_8(na, b->d_tabs, b->d_args, it, cnt, b->d_counter + na, smem, s));
+        b->ctx[order[0]]->n_launches += 1;
+    }
+    for (int i = 0; i < n; ++i) {
+        fc4_ctx *c = b->ctx[i];
+        if (!nms[i]) continue;
+        FC4_BCUDA(b, fc4::launch_reduce(c->t, args[i], channel_mask, unit_c3(), unit_c4(), gamma_out[i],
+                                        wp_out ? wp_out[i] : nullptr, counts_out ? counts_out[i] : nullptr,
+                                        c->stats, s));
+    }
+    return FC4_OK;
+}

@@ -8,4 +8,11 @@ cudaError_t launch4_f_1_4(int na, const Tables &t, const RateArgs &a, int ch, in
     return launch4_atoms<float, false, 1, 4>(na, t, a, ch, threads, s);
 }
 
+cudaError_t launch4_batch_f_1_4(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
+                                int *counter, size_t smem, cudaStream_t s) {
+    return launch4_batch_atoms<float, 1, 4>(na, tabs, args, items, n_items, counter, smem, s);
+}
+
+size_t general_smem_f(int na, const Tables &t) { return general_smem_atoms<float, 1, 8>(na, t); }
+
 }  // namespace fc4

@@ -8,4 +8,9 @@ cudaError_t launch4_f_5_8(int na, const Tables &t, const RateArgs &a, int ch, in
     return launch4_atoms<float, false, 5, 8>(na, t, a, ch, threads, s);
 }
 
+cudaError_t launch4_batch_f_5_8(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
+                                int *counter, size_t smem, cudaStream_t s) {
+    return launch4_batch_atoms<float, 5, 8>(na, tabs, args, items, n_items, counter, smem, s);
+}
+
 }  // namespace fc4

@@ -56,3 +56,58 @@ def test_large_cells_against_oracle(seed, mesh):
         g, wp, cnt = e.rates(300.0, 0.1, 31, q_subset=sub)
         assert np.array_equal(cnt.cpu().numpy(), CNT)
         assert_close(g.cpu().numpy(), G, tol, floor_frac=1e-6 if prec else 1e-12, what=f"na{c.n_atoms} p{prec}")
+
+
+def _jobs(n, scale=2):
+    from paper_2510_00518_gb300 import Engine, MIXED
+    jobs = []
+    for seed in range(n):
+        c, mesh = batch_crystal(seed)
+        mesh = tuple(max(2, m // scale) for m in mesh)
+        e = Engine(c, *morse_ifcs(c, seed=seed), mesh, precision=MIXED)
+        jobs.append((e, sample_q(int(np.prod(mesh)), 1, seed=seed)))
+    return jobs
+
+
+def test_persistent_batch_equals_per_context_kernels():
+    """One persistent launch per cell size over all crystals' units gives, for every crystal, the
+    Γ, WP and counts of its own general-kernel call (fc4_rates_static, same arithmetic) bit for bit;
+    the captured graph replays it exactly."""
+    from paper_2510_00518_gb300 import Batch
+    from paper_2510_00518_gb300.batch import BatchRunner
+    jobs = _jobs(8)
+    ref = []
+    for e, qs in jobs:
+        e.set_block_threads(128)
+        ref.append([x.clone() for x in e.rates_static(300.0, 0.1, 31, qs)])
+    outs = Batch([e for e, _ in jobs]).rates(300.0, 0.1, 31, q_subsets=[q for _, q in jobs])
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        for a, b in zip(o, r):
+            assert torch.equal(a, b)
+    runner = BatchRunner(jobs, 300.0, 0.1, 31, persistent=True)
+    for _ in range(2):
+        out = runner.run()
+        torch.cuda.synchronize()
+        for a, r in zip(out, ref):
+            assert torch.equal(a, r[0])
+
+
+def test_persistent_batch_against_oracle():
+    """Cells of 2, 6 and 8 atoms in one batch against the oracle (mixed bar)."""
+    from paper_2510_00518_gb300 import Batch, Engine, MIXED
+    cases = [(0, (3, 3, 3), [4]), (2, (1, 1, 2), [1]), (3, (1, 1, 1), [0])]
+    engines, qsets, refs = [], [], []
+    for seed, mesh, sub in cases:
+        c, _ = batch_crystal(seed)
+        sysm = (c,) + morse_ifcs(c, seed=seed)
+        prob = oracle.Problem(*sysm, mesh)
+        e = Engine(*sysm, mesh, precision=MIXED)
+        e.set_modes(prob.modes.omega, prob.modes.vel, prob.modes.evec)
+        engines.append(e)
+        qsets.append(sub)
+        refs.append(prob.rates(modes_of(sub, c.nb)))
+    outs = Batch(engines).rates(300.0, 0.1, 31, q_subsets=qsets)
+    for (g, wp, cnt), (G, WP, CNT) in zip(outs, refs):
+        assert np.array_equal(cnt.cpu().numpy(), CNT)
+        assert_close(g.cpu().numpy(), G, 1e-4, floor_frac=1e-6, what="batch")

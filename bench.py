@@ -250,9 +250,13 @@ def clocks_stop(p, f, gpu_index):
 # ------------------------------------------------------------------------------ GPU arm
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per (λ, q') unit of the tiled 4ph
-# kernels, from ncu captures of the same kernels on small cases (see profiles/); key (workload
-# kind, channel).  The bytes are the per-unit W reads, so they scale with the unit count.
-TRAFFIC_PER_UNIT = {("fixed", "4ph+-"): (4.109239e9 + 19.932e6) / 279936}
+# kernels, from ncu captures of the same kernels on small cases (fixed σ: 6x6x6 all modes; adaptive
+# σ: 8x8x8, 30 modes; see profiles/); key (window kind, channel).  The bytes are the per-unit W
+# reads, so they scale with the unit count.
+TRAFFIC_PER_UNIT = {("fixed", "4ph+-"): (4.109239e9 + 19.932e6) / 279936,
+                    ("adaptive", "4ph+-"): (227.183872e6 + 4.224768e6) / 15360,
+                    ("adaptive", "4ph++"): (228.271872e6 + 4.289792e6) / 15360,
+                    ("adaptive", "4ph--"): (228.271872e6 + 4.289792e6) / 15360}
 
 
 def flops_alg(stats, info, nb, adaptive):

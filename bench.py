@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--no-allmodes", action="store_true", help="skip the 8x8x8 all-modes line")
     p.add_argument("--batch", action="store_true",
                    help="time the 24-crystal batch (6-24 branches) as one CUDA graph instead")
+    p.add_argument("--batch-q", type=int, default=4, help="--batch: sampled q points per crystal")
     p.add_argument("--cpu-qp", type=int, default=0, help="oracle sample: partners q' < cpu_qp")
     p.add_argument("--cpu-q", type=int, default=0, help="oracle sample: q points (x nb modes)")
     p.add_argument("--block-threads", type=int, default=0)
@@ -606,7 +607,7 @@ def run_batch(args):
     for seed in range(24):
         c, mesh = batch_crystal(seed)
         e = Engine(c, *morse_ifcs(c, seed=seed), mesh, precision=MIXED)
-        jobs.append((e, sample_q(int(np.prod(mesh)), 4, seed=seed)))
+        jobs.append((e, sample_q(int(np.prod(mesh)), args.batch_q, seed=seed)))
 
     def timed(runner):
         for _ in range(args.warmup):
@@ -631,7 +632,7 @@ def run_batch(args):
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": head["ms_per_step"], "higher_is_better": True, "dtype": "f32",
                       "data": "synthetic", "arms": res,
-                      "config": {"workload": "batch-24-morse-supercells-6to24-branches", "q_per_crystal": 4,
+                      "config": {"workload": "batch-24-morse-supercells-6to24-branches", "q_per_crystal": args.batch_q,
                                  "meshes": "12^3/10^3/8^3/6^3 for 2/4/6/8 atoms", "graph": "one CUDA graph launch",
                                  "four_phonon": "one persistent launch per cell size (fc4_batch_rates)",
                                  "l2": "not flushed (graph replays back to back)"}}))

@@ -1496,6 +1496,12 @@ extern "C" fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_val
         for (int ch = 0; ch < 5; ++ch)
             if ((channel_mask >> ch) & 1)
                 c->cand[ch] = (ch < 2 ? (long long)N * nb * nb : (long long)N * N * nb * nb * nb) * nm;
+        c->have_last = true;                   // fc4_stats, fc4_processes and the backward read these
+        c->last_T = T_K;
+        c->last_sigma = sigma_value;
+        c->last_adaptive = false;
+        c->last_mask = channel_mask;
+        c->last_modes = modes;
     }
     // three-phonon kernels per context (they set n_part of their channels)
     for (int i = 0; i < n; ++i) {

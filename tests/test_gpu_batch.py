@@ -35,7 +35,7 @@ def test_graph_batch_matches_eager(tmp_path):
     assert bt in (64, 96, 128)
     assert autotune(jobs[3][0], 300.0, 0.1, 31, jobs[3][1], cache=cache) == bt   # cached
     eager = [e.rates(300.0, 0.1, 31, q_subset=qs)[0].clone() for e, qs in jobs]
-    runner = BatchRunner(jobs, 300.0, 0.1, 31)
+    runner = BatchRunner(jobs, 300.0, 0.1, 31, persistent=False)      # a graph of per-crystal calls
     for _ in range(2):
         out = runner.run()
         torch.cuda.synchronize()

@@ -383,14 +383,16 @@ fc4_status fc4_expand_irreducible(const int mesh[3], int nb, const int *rep, con
 
 /* ---------------------------------------------------------------- batches of crystals
  * Many contexts (crystals of different cell sizes, meshes and clusters) evaluated together.
- * fc4_batch_rates runs the four-phonon units (λ, q') of every context with the same cell size as
- * ONE persistent launch of the general kernel: a work list of (context, channel, unit) from the
- * largest meshes down, each 128-thread block taking the next item from a global counter, so that
- * the uneven per-crystal and per-q work balances across the whole GPU; three-phonon kernels and
- * reductions run per context.  FP32 contractions (contexts of any precision but FC4_FP64), fixed
- * σ, no tensor cores; Γ, WP and counts equal those of fc4_rates_static on each context (the same
- * kernel arithmetic).  After a first call with the same arguments (which sizes every buffer), a
- * call performs only stream-ordered launches and memsets, so it can be captured in a CUDA graph. */
+ * fc4_batch_rates runs the four-phonon units (λ, q') of every context of more than two atoms with
+ * the same cell size as ONE persistent launch of the general kernel: a work list of (context,
+ * channel, unit) from the largest meshes down, each 128-thread block taking the next item from a
+ * global counter, so that the uneven per-crystal and per-q work balances across the whole GPU;
+ * their three-phonon kernels and reductions run per context, FP32 contractions, no tensor cores,
+ * and their Γ, WP and counts equal fc4_rates_static's (the same kernel arithmetic).  Contexts of up
+ * to two atoms run their own fc4_rates (the tiled kernels, several times faster than the general
+ * one on such cells).  Contexts of any precision but FC4_FP64; fixed σ.  After a first call with the
+ * same arguments (which sizes every buffer), a call performs only stream-ordered launches and
+ * memsets, so it can be captured in a CUDA graph. */
 
 typedef struct fc4_batch fc4_batch;
 

@@ -1429,6 +1429,19 @@ extern "C" fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_val
     for (int i = 0; i < n; ++i) {
         fc4_ctx *c = b->ctx[i];
         if (c->precision == FC4_FP64) return bfail(b, FC4_ERR_INVALID, "fc4_batch_rates: FP32 contexts only");
+        // cells the tiled kernels serve (up to two atoms, W buffer) keep their own, faster path
+        if (fc4::rates4_wbuf_per_mode(c->t, 0)) {
+            nms[i] = 0;
+            const int nq = q_subsets && q_subsets[i] ? n_q[i] : 0;
+            if (q_subsets && q_subsets[i] && (!n_q || nq < 0))
+                return bfail(b, FC4_ERR_INVALID, "n_q required with q_subsets");
+            const fc4_status st = rates_call(c, T_K, 0, sigma_value, channel_mask,
+                                             q_subsets && q_subsets[i] ? q_subsets[i] : nullptr, nq, gamma_out[i],
+                                             wp_out ? wp_out[i] : nullptr, counts_out ? counts_out[i] : nullptr,
+                                             stream, nullptr, nullptr);
+            if (st != FC4_OK) return bfail(b, st, c->last_error);
+            continue;
+        }
         const int N = c->t.N, nb = c->t.nb;
         std::vector<int> modes;
         if (q_subsets && q_subsets[i]) {

@@ -241,8 +241,9 @@ fc4_status fc4_kappa_backward(fc4_ctx *ctx, double T_K, const double *gamma, int
 
 /* fc4_rates_backward - gradient of L = Σ_{ch,i} dL_dgamma[ch][i] Γ_ch(i) with respect to every
  * stored Φ3 and Φ4 entry (entries independent), at fixed modes and σ (fixed or adaptive: both
- * depend on the modes only), for the (T, σ, mask, subset) of the last fc4_rates call, in FP64
- * whatever the context's precision:
+ * depend on the modes only), for the (T, σ, mask, subset) of the last fc4_rates call.  FP64 in
+ * an FC4_FP64 context; otherwise the 4ph terms run in FP32 (V recomputed in FP32, per-mode slices
+ * accumulated as FP32 Kahan pairs, summed in FP64) and the 3ph terms in FP64:
  *   dL/dΦ_c = Σ_processes dL/dΓ C/N^k w 2 Re(conj(V) dV/dΦ_c),  V recomputed (not stored).
  * Deterministic (fixed summation order).  dL_dgamma: device [5][n_q*nb]; dphi3: device
  * [nc3][27]; dphi4: device [nc4][81], in the cluster order given to fc4_init (overwritten;

@@ -1056,13 +1056,15 @@ fc4_status fc4_rates_backward(fc4_ctx *c, const double *dL_dgamma, double *dphi3
         if (ch < 2 && (!dphi3 || !c->nc3)) continue;
         if (ch >= 2 && (!dphi4 || !c->nc4)) continue;
         const double cst = ch < 2 ? unit_c3() / N : unit_c4() / (N * N);
-        FC4_CUDA(c, fc4::launch_adjoint(c->t, a, ch, dL_dgamma, cst, c->adj_part, s));
+        // 3ph: FP64 always; 4ph: FP64 in an FP64 context, else FP32 (FP64 accumulation of the slices)
+        const int fp64 = ch < 2 || c->precision == FC4_FP64;
+        FC4_CUDA(c, fc4::launch_adjoint(c->t, a, ch, dL_dgamma, cst, c->adj_part, fp64, s));
         c->n_launches += 1;
         if (ch < 2) {
-            FC4_CUDA(c, fc4::launch_sum_slices(nm, 27 * c->nc3, c->adj_part, dphi3, first3 ? 0 : 1, s));
+            FC4_CUDA(c, fc4::launch_sum_slices(nm, 27 * c->nc3, c->adj_part, dphi3, first3 ? 0 : 1, 0, s));
             first3 = false;
         } else {
-            FC4_CUDA(c, fc4::launch_sum_slices(nm, 81 * c->nc4, c->adj_part, c->adj_tmp, first4 ? 0 : 1, s));
+            FC4_CUDA(c, fc4::launch_sum_slices(nm, 81 * c->nc4, c->adj_part, c->adj_tmp, first4 ? 0 : 1, !fp64, s));
             first4 = false;
         }
         c->n_launches += 1;

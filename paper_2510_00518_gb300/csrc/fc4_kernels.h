@@ -162,10 +162,11 @@ cudaError_t launch_kappa(const Tables &t, double hbar_over_kT, double kB, const 
 cudaError_t launch_kappa_backward(const Tables &t, double hbar_over_kT, double kB, const double *gamma,
                                   int mask, double scale, const double *dLdk, double *dLdg, cudaStream_t s);
 cudaError_t launch_unpermute(int nc, int width, const int *perm, const double *in, double *out, cudaStream_t s);
+// fp64 = 0: the 4ph adjoint in FP32 (slices of FP32 Kahan pairs; sum them with kahan32 = 1)
 cudaError_t launch_adjoint(const Tables &t, const RateArgs &a, int ch, const double *dLdG, double cst,
-                           double *part, cudaStream_t s);
+                           double *part, int fp64, cudaStream_t s);
 cudaError_t launch_sum_slices(int n_slices, int n, const double *part, double *out, int accumulate,
-                              cudaStream_t s);
+                              int kahan32, cudaStream_t s);
 cudaError_t launch_count_processes(const Tables &t, const RateArgs &a, int ch, int mode, int *counts,
                                    cudaStream_t s);
 cudaError_t launch_write_processes(const Tables &t, const RateArgs &a, int ch, int mode,

@@ -16,27 +16,40 @@
 //
 // Three-phonon: one block per mode λ; processes are compacted per round in the same way and
 // the owner of each Φ3 entry adds 2 Re(G conj(V) phase_c e_λ e^s' e*'' / sqrt(m)) in order.
-#include "fc4_window.cuh"
+#include "k_rates4.cuh"
 
 namespace fc4 {
 
 constexpr int kAdjThreads = 128;
 
+// Kahan-compensated FP32 accumulation in a (sum, compensation) pair (mixed-precision slices)
+__device__ __forceinline__ void kahan_add(float2 &acc, float x) {
+    const float y = x - acc.y;
+    const float t = acc.x + y;
+    acc.y = (t - acc.x) - y;
+    acc.x = t;
+}
+
 // ------------------------------------------------------------------------------ four-phonon
 
-template <int NA>
+template <typename R, int NA>
 struct Item4 {
     int q2, q3;
-    double2 ybar[3 * NA];
-    double2 e3c[3 * NA];
+    Cplx<R> ybar[3 * NA];
+    Cplx<R> e3c[3 * NA];
 };
 
-template <int NA>
+template <typename R, int NA>
 __global__ void __launch_bounds__(kAdjThreads)
 adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
             const double *__restrict__ dLdG, double cst, double *dphi_part) {
     constexpr int NB = 3 * NA;
-    using C = double2;
+    using C = Cplx<R>;
+    const C *ev = Sel<R>::ev(t);
+    const C *rt = Sel<R>::rt(t);
+    const C *P4 = Sel<R>::P4(t);
+    const R *phi4 = Sel<R>::phi4(t);
+    const R *ism4 = Sel<R>::ism4(t);
     const int s1 = (ch == 4) ? -1 : 1;
     const int s2 = (ch == 2) ? 1 : -1;
     const int N = t.N, nk = t.n_keys, nc4 = t.nc4;
@@ -47,21 +60,26 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
     C *sPh = sCon + nc4 * 9;                                    // [nc4] phase / sqrt(m) at (q, q')
     C *sE = sPh + nc4;                                          // [NA*NA][9]
     C *se0 = sE + NA * NA * 9;                                  // [NB]
-    Item4<NA> *sIt = reinterpret_cast<Item4<NA> *>(se0 + NB);   // [kAdjThreads]
+    Item4<R, NA> *sIt = reinterpret_cast<Item4<R, NA> *>(se0 + NB);   // [kAdjThreads]
     __shared__ int s_scan[32];
     __shared__ int s_max;
 
     const int ms = blockIdx.x;
     const int m0 = a.modes[ms];
     const int q0 = m0 / NB, j0 = m0 - q0 * NB;
+    // per-mode gradient slice: FP64, or (mixed) FP32 Kahan pairs (sum, compensation) in the same bytes
     double *dphi = dphi_part + (size_t)ms * nc4 * 81;
-    for (int k = threadIdx.x; k < nc4 * 81; k += kAdjThreads) dphi[k] = 0.0;
+    float2 *dphk = reinterpret_cast<float2 *>(dphi);
+    for (int k = threadIdx.x; k < nc4 * 81; k += kAdjThreads) {
+        if constexpr (sizeof(R) == 8) dphi[k] = 0.0;
+        else dphk[k] = make_float2(0.0f, 0.0f);
+    }
     const double gl = dLdG[(size_t)ch * a.n_modes + ms] * cst;
     if ((q0 == 0 && j0 < 3) || gl == 0.0) return;
     const int4 c0 = t.qc[q0];
     const double w0 = t.om[m0];
     const float w0f = t.om32[m0];
-    for (int k = threadIdx.x; k < NB; k += kAdjThreads) se0[k] = t.ev[(q0 * NB + k) * NB + j0];
+    for (int k = threadIdx.x; k < NB; k += kAdjThreads) se0[k] = ev[(q0 * NB + k) * NB + j0];
 
     for (int q1 = 0; q1 < N; ++q1) {
         const int4 c1 = t.qc[q1];
@@ -76,18 +94,18 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                 const int ab = k / 9, ij = k - ab * 9;
                 const int at = ab / NA, bt = ab - at * NA;
                 const int al = ij / 3, be = ij - al * 3;
-                sE[k] = cmul(se0[3 * at + al], cconj_if(t.ev[(q1 * NB + 3 * bt + be) * NB + j1], s1 < 0));
+                sE[k] = cmul(se0[3 * at + al], cconj_if(ev[(q1 * NB + 3 * bt + be) * NB + j1], s1 < 0));
             }
             for (int c = threadIdx.x; c < nc4; c += kAdjThreads) {
-                const C p = t.rt[mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) - phase_index(c0, t.c4_r3[c], t.L), t.L)];
-                sPh[c] = cmake(p.x * t.c4_ism[c], p.y * t.c4_ism[c]);
+                const C p = rt[mod_pos(s1 * phase_index(c1, t.c4_r13[c], t.L) - phase_index(c0, t.c4_r3[c], t.L), t.L)];
+                sPh[c] = cmake(p.x * ism4[c], p.y * ism4[c]);
             }
             for (int k = threadIdx.x; k < nk * 9; k += kAdjThreads) sH[k] = czero<C>();
             __syncthreads();
             for (int k = threadIdx.x; k < nc4 * 9; k += kAdjThreads) {
                 const int c = k / 9, gd = k - c * 9;
                 const int4 at = t.c4_at[c];
-                const double *ph4 = t.phi4 + 81 * c + gd;
+                const R *ph4 = phi4 + 81 * c + gd;
                 const C *E = sE + (at.x * NA + at.y) * 9;
                 C v = czero<C>();
 #pragma unroll
@@ -146,16 +164,16 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                         if (mask[next_j3]) j3 = next_j3;
                         ++next_j3;
                     }
-                    Item4<NA> it;
+                    Item4<R, NA> it;
                     if (j3 >= 0) {
                         C Y[NA][3];
                         for (int c = 0; c < NA; ++c)
                             for (int g = 0; g < 3; ++g) Y[c][g] = czero<C>();
-                        const C *P = t.P4 + (size_t)q2 * nk;
+                        const C *P = P4 + (size_t)q2 * nk;
                         for (int c = 0; c < NA; ++c)
                             for (int d = 0; d < NA; ++d) {
                                 C e3[3];
-                                for (int dl = 0; dl < 3; ++dl) e3[dl] = cconj(t.ev[(q3 * NB + 3 * d + dl) * NB + j3]);
+                                for (int dl = 0; dl < 3; ++dl) e3[dl] = cconj(ev[(q3 * NB + 3 * d + dl) * NB + j3]);
                                 for (int r = t.grp_start[c * NA + d]; r < t.grp_start[c * NA + d + 1]; ++r) {
                                     const C ph = cconj_if(P[r], s2 < 0);
                                     const C *Wr = sW + 9 * r;
@@ -175,7 +193,7 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                             m &= m - 1;
                             const int m2 = q2 * NB + j2;
                             C e2[NB];
-                            for (int k = 0; k < NB; ++k) e2[k] = cconj_if(t.ev[(q2 * NB + k) * NB + j2], s2 < 0);
+                            for (int k = 0; k < NB; ++k) e2[k] = cconj_if(ev[(q2 * NB + k) * NB + j2], s2 < 0);
                             C V = czero<C>();
                             for (int c = 0; c < NA; ++c)
                                 for (int g = 0; g < 3; ++g) V = cfma(e2[3 * c + g], Y[c][g], V);
@@ -185,12 +203,12 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                             const double w = (ch == 4 ? 1.0 / 6.0 : 0.5) *
                                              occupation_factor<double>(ch, t.occ[m1], t.occ[m2], t.occ[m3]) * gs *
                                              t.invw[m0] * t.invw[m1] * t.invw[m2] * t.invw[m3];
-                            const C f = cmake(gl * w * V.x, -gl * w * V.y);      // G conj(V)
+                            const C f = cmake((R)(gl * w * (double)V.x), (R)(-gl * w * (double)V.y));      // G conj(V)
                             for (int k = 0; k < NB; ++k) it.ybar[k] = cfma(f, e2[k], it.ybar[k]);
                         }
                         it.q2 = q2;
                         it.q3 = q3;
-                        for (int k = 0; k < NB; ++k) it.e3c[k] = cconj(t.ev[(q3 * NB + k) * NB + j3]);
+                        for (int k = 0; k < NB; ++k) it.e3c[k] = cconj(ev[(q3 * NB + k) * NB + j3]);
                     }
                     int total;
                     const int off = block_exclusive_scan(j3 >= 0 ? 1 : 0, s_scan, &total);
@@ -204,7 +222,7 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                         const int cc = grp / NA, dd = grp - cc * NA;
                         C h = sH[k];
                         for (int i = 0; i < total; ++i) {
-                            const C ph = cconj_if(t.P4[(size_t)sIt[i].q2 * nk + r], s2 < 0);
+                            const C ph = cconj_if(P4[(size_t)sIt[i].q2 * nk + r], s2 < 0);
                             h = cfma(cmul(ph, sIt[i].ybar[3 * cc + g]), sIt[i].e3c[3 * dd + dl], h);
                         }
                         sH[k] = h;
@@ -220,7 +238,8 @@ adj4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
                     for (int k = threadIdx.x; k < 81; k += kAdjThreads) {
                         const int ab = k / 9, gd = k - ab * 9;
                         const C z = cmul(cmul(sPh[c], sE[(at.x * NA + at.y) * 9 + ab]), sH[r * 9 + gd]);
-                        dphi[(size_t)c * 81 + k] += 2.0 * z.x;
+                        if constexpr (sizeof(R) == 8) dphi[(size_t)c * 81 + k] += 2.0 * z.x;
+                        else kahan_add(dphk[(size_t)c * 81 + k], 2.0f * z.x);
                     }
                 }
         }
@@ -340,46 +359,61 @@ adj3_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a
 
 // ------------------------------------------------------------------------------ slices -> gradient
 
-__global__ void sum_slices_kernel(int n_slices, int n, const double *part, double *out, int accumulate) {
+__global__ void sum_slices_kernel(int n_slices, int n, const double *part, double *out, int accumulate,
+                                  int kahan32) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     double s = accumulate ? out[k] : 0.0;
-    for (int i = 0; i < n_slices; ++i) s += part[(size_t)i * n + k];
+    if (kahan32) {                                       // FP32 (sum, compensation) pairs
+        const float2 *p = reinterpret_cast<const float2 *>(part);
+        for (int i = 0; i < n_slices; ++i) {
+            const float2 v = p[(size_t)i * n + k];
+            s += (double)v.x - (double)v.y;
+        }
+    } else {
+        for (int i = 0; i < n_slices; ++i) s += part[(size_t)i * n + k];
+    }
     out[k] = s;
 }
 
 template <int NA>
 static cudaError_t launch_adj_na(const Tables &t, const RateArgs &a, int ch, const double *dLdG, double cst,
-                                 double *part, cudaStream_t s) {
+                                 double *part, int fp64, cudaStream_t s) {
     if (a.n_modes == 0) return cudaSuccess;
     if (ch < 2) {
         adj3_kernel<NA><<<a.n_modes, kAdjThreads, 0, s>>>(t, a, ch, dLdG, cst, part);
-    } else {
-        constexpr int NB = 3 * NA;
-        const size_t smem = sizeof(double2) * ((size_t)t.n_keys * 18 + (size_t)t.nc4 * 10 + NA * NA * 9 + NB) +
-                            sizeof(Item4<NA>) * kAdjThreads + 16;
-        cudaError_t e = cudaFuncSetAttribute(adj4_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        adj4_kernel<NA><<<a.n_modes, kAdjThreads, smem, s>>>(t, a, ch, dLdG, cst, part);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    auto run = [&](auto zero) -> cudaError_t {
+        using R = decltype(zero);
+        using C = Cplx<R>;
+        constexpr int NB = 3 * NA;
+        const size_t smem = sizeof(C) * ((size_t)t.n_keys * 18 + (size_t)t.nc4 * 10 + NA * NA * 9 + NB) +
+                            sizeof(Item4<R, NA>) * kAdjThreads + 16;
+        cudaError_t e = cudaFuncSetAttribute(adj4_kernel<R, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        adj4_kernel<R, NA><<<a.n_modes, kAdjThreads, smem, s>>>(t, a, ch, dLdG, cst, part);
+        return cudaGetLastError();
+    };
+    return fp64 ? run(0.0) : run(0.0f);
 }
 
 cudaError_t launch_adjoint(const Tables &t, const RateArgs &a, int ch, const double *dLdG, double cst,
-                           double *part, cudaStream_t s) {
+                           double *part, int fp64, cudaStream_t s) {
     switch (t.n_atoms) {
-    case 1: return launch_adj_na<1>(t, a, ch, dLdG, cst, part, s);
-    case 2: return launch_adj_na<2>(t, a, ch, dLdG, cst, part, s);
-    case 3: return launch_adj_na<3>(t, a, ch, dLdG, cst, part, s);
-    case 4: return launch_adj_na<4>(t, a, ch, dLdG, cst, part, s);
+    case 1: return launch_adj_na<1>(t, a, ch, dLdG, cst, part, fp64, s);
+    case 2: return launch_adj_na<2>(t, a, ch, dLdG, cst, part, fp64, s);
+    case 3: return launch_adj_na<3>(t, a, ch, dLdG, cst, part, fp64, s);
+    case 4: return launch_adj_na<4>(t, a, ch, dLdG, cst, part, fp64, s);
     default: return cudaErrorInvalidValue;       // cells of more than 4 atoms: not instantiated
     }
 }
 
 cudaError_t launch_sum_slices(int n_slices, int n, const double *part, double *out, int accumulate,
-                              cudaStream_t s) {
+                              int kahan32, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    sum_slices_kernel<<<(n + 255) / 256, 256, 0, s>>>(n_slices, n, part, out, accumulate);
+    sum_slices_kernel<<<(n + 255) / 256, 256, 0, s>>>(n_slices, n, part, out, accumulate, kahan32);
     return cudaGetLastError();
 }
 

@@ -148,3 +148,20 @@ def test_rates_gradient_8cubed_finite_differences(sysm):
             assert abs(fd - an) <= 1e-6 * abs(an) + noise, (order, c, x, fd, an, noise)
     finally:
         e.update_anharmonic(p3, p4)
+
+
+@pytest.mark.parametrize("mesh,sub", [((3, 3, 3), [13]), ((4, 4, 4), [22])])
+def test_rates_backward_mixed_precision(sysm, mesh, sub):
+    """The mixed-precision adjoint (4ph terms in FP32 with FP32 Kahan slices summed in FP64; 3ph in
+    FP64) against the oracle's FP64 gradient: 3ph to 1e-8 elementwise, 4ph to 1e-4 of the largest
+    gradient entry (normwise: single entries are sums with cancellation)."""
+    prob = oracle.Problem(*sysm, mesh)
+    e = make_engine(sysm, mesh, precision=1, prob=prob)
+    modes = modes_of(sub, 6)
+    dL = np.random.default_rng(11).standard_normal((5, modes.size))
+    e.rates(300.0, 0.1, 31, q_subset=sub)
+    d3, d4 = e.backward(torch.tensor(dL, device="cuda"))
+    g3, g4 = prob.grad(modes, dL)
+    assert_close(d3.cpu().numpy().reshape(-1), g3.reshape(-1), 1e-8, floor_frac=1e-9, what="dphi3 (mixed context)")
+    err = np.abs(d4.cpu().numpy() - g4).max() / np.abs(g4).max()
+    assert err <= 1e-4, err

@@ -313,7 +313,8 @@ fc4_status fc4_set_sampling(fc4_ctx *ctx, double fraction, unsigned long long se
  * bit 0: no compaction - each thread evaluates the (q'', j') entries its own window test found, as
  * an uncompacted GPU-only loop does (the paper's Algorithm 2 and its warp divergence, Results),
  * instead of the block's entries being dealt out to all threads in order.  0 (the default)
- * restores compaction.  Other bits return FC4_ERR_INVALID. */
+ * restores compaction.  Mixed-precision tiled kernels only (others ignore it).  Other bits return
+ * FC4_ERR_INVALID. */
 fc4_status fc4_set_ablation(fc4_ctx *ctx, int flags);
 
 /* fc4_set_precision - change the arithmetic of later fc4_rates calls (any fc4_precision; the
@@ -391,7 +392,9 @@ fc4_status fc4_expand_irreducible(const int mesh[3], int nb, const int *rep, con
  * their three-phonon kernels and reductions run per context, FP32 contractions, no tensor cores,
  * and their Γ, WP and counts equal fc4_rates_static's (the same kernel arithmetic).  Contexts of up
  * to two atoms run their own fc4_rates (the tiled kernels, several times faster than the general
- * one on such cells).  Contexts of any precision but FC4_FP64; fixed σ.  After a first call with the
+ * one on such cells).  Contexts of any precision but FC4_FP64; fixed σ; at most 40 contexts.  The
+ * contexts' tables and call arguments go to the kernel's constant memory, one copy per process and
+ * device: calls of different batches that overlap on the GPU race.  After a first call with the
  * same arguments (which sizes every buffer), a call performs only stream-ordered launches and
  * memsets, so it can be captured in a CUDA graph. */
 

@@ -1350,9 +1350,7 @@ extern "C" fc4_status fc4_rates_static(fc4_ctx *c, double T_K, double sigma_valu
 
 struct fc4_batch {
     std::vector<fc4_ctx *> ctx;
-    fc4::Tables *d_tabs = nullptr;
-    fc4::RateArgs *d_args = nullptr;
-    std::vector<fc4::RateArgs> args_on_device;
+    std::vector<fc4::Tables> tabs;             // host copies of the contexts' tables
     int4 *d_items = nullptr;
     size_t items_cap = 0;
     std::vector<int4> items_on_device;
@@ -1361,6 +1359,10 @@ struct fc4_batch {
 };
 
 namespace {
+
+// content last copied into the batch kernels' constant memory (shared by every batch)
+std::vector<unsigned char> g_batch_meta;
+std::mutex g_batch_mu;
 
 fc4_status bfail(fc4_batch *b, fc4_status s, const std::string &msg) {
     if (b) b->last_error = msg;
@@ -1388,12 +1390,12 @@ fc4_status fc4_batch_create(fc4_ctx *const *ctxs, int n, fc4_batch **out) {
         if (!ctxs[i]) { delete b; return bfail(nullptr, FC4_ERR_INVALID, "fc4_batch_create: NULL context"); }
         b->ctx.push_back(ctxs[i]);
     }
-    std::vector<fc4::Tables> tabs;
-    for (fc4_ctx *c : b->ctx) tabs.push_back(c->t);
-    cudaError_t e = cudaMalloc((void **)&b->d_tabs, sizeof(fc4::Tables) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, sizeof(fc4::RateArgs) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, sizeof(int) * 9);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_tabs, tabs.data(), sizeof(fc4::Tables) * n, cudaMemcpyHostToDevice);
+    if (n > fc4::kMaxBatch) {
+        delete b;
+        return bfail(nullptr, FC4_ERR_INVALID, "fc4_batch_create: more than 40 contexts");
+    }
+    for (fc4_ctx *c : b->ctx) b->tabs.push_back(c->t);
+    cudaError_t e = cudaMalloc((void **)&b->d_counter, sizeof(int) * 9);
     if (e != cudaSuccess) {
         fc4_batch_destroy(b);
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? FC4_ERR_OOM : FC4_ERR_CUDA,
@@ -1407,8 +1409,6 @@ const char *fc4_batch_last_error(const fc4_batch *b) { return b ? b->last_error.
 
 void fc4_batch_destroy(fc4_batch *b) {
     if (!b) return;
-    cudaFree(b->d_tabs);
-    cudaFree(b->d_args);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
     delete b;
@@ -1547,10 +1547,16 @@ extern "C" fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_val
         classes.back()[2] = (long long)items.size() - classes.back()[1];
     }
     if (items.size() > 0x7fffffffULL) return bfail(b, FC4_ERR_INVALID, "fc4_batch_rates: too many units");
-    if (args.size() != b->args_on_device.size() ||
-        std::memcmp(args.data(), b->args_on_device.data(), sizeof(fc4::RateArgs) * args.size()) != 0) {
-        FC4_BCUDA(b, cudaMemcpyAsync(b->d_args, args.data(), sizeof(fc4::RateArgs) * n, cudaMemcpyHostToDevice, s));
-        b->args_on_device = args;
+    {   // tables and arguments into the constant memory of both kernel units, when they changed
+        std::vector<unsigned char> blob(sizeof(fc4::Tables) * n + sizeof(fc4::RateArgs) * n);
+        std::memcpy(blob.data(), b->tabs.data(), sizeof(fc4::Tables) * n);
+        std::memcpy(blob.data() + sizeof(fc4::Tables) * n, args.data(), sizeof(fc4::RateArgs) * n);
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        if (blob != g_batch_meta) {
+            FC4_BCUDA(b, fc4::batch_upload_f_1_4(b->tabs.data(), args.data(), n, s));
+            FC4_BCUDA(b, fc4::batch_upload_f_5_8(b->tabs.data(), args.data(), n, s));
+            g_batch_meta = blob;
+        }
     }
     if (items.size() != b->items_on_device.size() ||
         std::memcmp(items.data(), b->items_on_device.data(), sizeof(int4) * items.size()) != 0) {
@@ -1573,8 +1579,8 @@ extern "C" fc4_status fc4_batch_rates(fc4_batch *b, double T_K, double sigma_val
         FC4_BCUDA(b, cudaMemsetAsync(b->d_counter + na, 0, sizeof(int), s));
         const int4 *it = b->d_items + classes[k][1];
         const int cnt = (int)classes[k][2];
-        FC4_BCUDA(b, na <= 4 ? fc4::launch4_batch_f_1_4(na, b->d_tabs, b->d_args, it, cnt, b->d_counter + na, smem, s)
-                             : fc4::launch4_batch_f_5_8(na, b->d_tabs, b->d_args, it, cnt, b->d_counter + na, smem, s));
+        FC4_BCUDA(b, na <= 4 ? fc4::launch4_batch_f_1_4(na, it, cnt, b->d_counter + na, smem, s)
+                             : fc4::launch4_batch_f_5_8(na, it, cnt, b->d_counter + na, smem, s));
         b->ctx[order[0]]->n_launches += 1;
     }
     for (int i = 0; i < n; ++i) {

@@ -123,11 +123,13 @@ bool tc_supported(const Tables &t);
 cudaError_t launch_rates4_tc(const Tables &t, const RateArgs &a, int ch, int mode0, int nm, const float2 *w,
                              cudaStream_t s);
 // batched persistent 4ph launch over many contexts of one cell size (FP32, fixed σ): work items
-// (context, channel, unit); tabs / args: device arrays indexed by context
-cudaError_t launch4_batch_f_1_4(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s);
-cudaError_t launch4_batch_f_5_8(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s);
+// (context, channel, unit); the contexts' tables and arguments are uploaded first into the constant
+// memory of both translation units (atoms 1-4 and 5-8), at most kMaxBatch contexts
+constexpr int kMaxBatch = 40;
+cudaError_t launch4_batch_f_1_4(int na, const int4 *items, int n_items, int *counter, size_t smem, cudaStream_t s);
+cudaError_t launch4_batch_f_5_8(int na, const int4 *items, int n_items, int *counter, size_t smem, cudaStream_t s);
+cudaError_t batch_upload_f_1_4(const Tables *tabs, const RateArgs *args, int n, cudaStream_t s);
+cudaError_t batch_upload_f_5_8(const Tables *tabs, const RateArgs *args, int n, cudaStream_t s);
 size_t general_smem_f(int na, const Tables &t);
 // bytes of W scratch the tiled 4ph path needs per mode (0 if the general kernel is used)
 size_t rates4_wbuf_per_mode(const Tables &t, int fp64);

@@ -464,26 +464,6 @@ rates4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs
     rates4_unit<R, NA, ADA>(t, a, ch, blockIdx.x);
 }
 
-// Persistent form over many contexts of one cell size: each block takes the next work item
-// (context, channel, unit) from the list in order (a global counter, zeroed before the launch)
-// until the list is exhausted.  The list puts the costliest units first.  Tables and per-call
-// arguments of each context sit in device memory.
-template <typename R, int NA>
-__global__ void __launch_bounds__(128, 4)
-rates4_batch_kernel(const Tables *__restrict__ tabs, const RateArgs *__restrict__ args,
-                    const int4 *__restrict__ items, int n_items, int *counter) {
-    __shared__ int s_item;
-    for (;;) {
-        __syncthreads();                                 // the previous unit is done with shared memory
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int i = s_item;
-        if (i >= n_items) break;
-        const int4 it = items[i];                        // (context, channel, unit, -)
-        rates4_unit<R, NA, false>(tabs[it.x], args[it.x], it.y, it.z);
-    }
-}
-
 template <typename R, int NA, bool ADA>
 cudaError_t launch4(const Tables &t, const RateArgs &a, int ch, int threads, cudaStream_t s) {
     using C = Cplx<R>;
@@ -511,32 +491,6 @@ size_t general_smem_bytes(const Tables &t) {
     size_t smem = sizeof(C) * ((size_t)t.n_keys * 9 + (size_t)t.nc4 * 9 + NA * NA * 9 + NB) +
                   sizeof(C) + sizeof(unsigned long long) * (size_t)kQChunk;
     return (smem + 15) & ~size_t(15);
-}
-
-// The persistent batch kernel on a grid that fills the device (blocks resident per SM x SMs).
-template <typename R, int NA>
-cudaError_t launch4_batch(const Tables *tabs, const RateArgs *args, const int4 *items, int n_items, int *counter,
-                          size_t smem, cudaStream_t s) {
-    if (n_items <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rates4_batch_kernel<R, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rates4_batch_kernel<R, NA>, 128, smem)) != cudaSuccess)
-        return e;
-    const int grid = std::max(1, std::min(n_items, sms * std::max(per_sm, 1)));
-    rates4_batch_kernel<R, NA><<<grid, 128, smem, s>>>(tabs, args, items, n_items, counter);
-    return cudaGetLastError();
-}
-
-template <typename R, int NA, int HI>
-cudaError_t launch4_batch_atoms(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s) {
-    if (na == NA) return launch4_batch<R, NA>(tabs, args, items, n_items, counter, smem, s);
-    if constexpr (NA < HI) return launch4_batch_atoms<R, NA + 1, HI>(na, tabs, args, items, n_items, counter, smem, s);
-    else return cudaErrorInvalidValue;
 }
 
 template <typename R, int NA, int HI>
@@ -568,11 +522,7 @@ FC4_GENERAL_LAUNCHER(launch4_ad_d_5_8)
 FC4_GENERAL_LAUNCHER(launch4_ad_f_1_4)
 FC4_GENERAL_LAUNCHER(launch4_ad_f_5_8)
 #undef FC4_GENERAL_LAUNCHER
-// batched persistent launchers (FP32, fixed σ), atoms 1-4 / 5-8
-cudaError_t launch4_batch_f_1_4(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s);
-cudaError_t launch4_batch_f_5_8(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s);
+
 // tiled-path launchers (<= 2 atoms)
 cudaError_t launch4_tile_f(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);
 cudaError_t launch4_tile_d(int na, const Tables &t, const RateArgs &a, int ch, cudaStream_t s);

@@ -1,6 +1,6 @@
 // k_rates4_f14.cu - instantiations of the fused four-phonon kernel (float, 1..4 atoms per cell,
 // fixed σ); split across translation units so that they compile in parallel.
-#include "k_rates4.cuh"
+#include "k_rates4_batch.cuh"
 
 namespace fc4 {
 
@@ -8,9 +8,13 @@ cudaError_t launch4_f_1_4(int na, const Tables &t, const RateArgs &a, int ch, in
     return launch4_atoms<float, false, 1, 4>(na, t, a, ch, threads, s);
 }
 
-cudaError_t launch4_batch_f_1_4(int na, const Tables *tabs, const RateArgs *args, const int4 *items, int n_items,
-                                int *counter, size_t smem, cudaStream_t s) {
-    return launch4_batch_atoms<float, 1, 4>(na, tabs, args, items, n_items, counter, smem, s);
+cudaError_t launch4_batch_f_1_4(int na, const int4 *items, int n_items, int *counter, size_t smem,
+                                cudaStream_t s) {
+    return launch4_batch_atoms<float, 1, 4>(na, items, n_items, counter, smem, s);
+}
+
+cudaError_t batch_upload_f_1_4(const Tables *tabs, const RateArgs *args, int n, cudaStream_t s) {
+    return batch_upload(tabs, args, n, s);
 }
 
 size_t general_smem_f(int na, const Tables &t) { return general_smem_atoms<float, 1, 8>(na, t); }

@@ -117,7 +117,7 @@ w4_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, 
 // BTE = true also accumulates the off-diagonal term of the iterative Boltzmann equation,
 //   Δ_λ = Σ_p γ_p Σ_k s_k (ω_k / ω_λ) F_k  (partner signs: ++ (-, -, +), +- (-, +, +), -- (+, +, +)),
 // into a.part_d; the partner combination is symmetric under the swap the triangular domain uses.
-template <typename R, int NA, bool ADA, int kQPT, bool BTE = false>
+template <typename R, int NA, bool ADA, int kQPT, bool BTE = false, bool NOCOMP = false>
 __global__ void __launch_bounds__(kTileQ, ADA ? 3 : 4)
 rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ RateArgs a, int ch,
                    int mode0, const Cplx<R> *__restrict__ wall) {
@@ -330,11 +330,12 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
             for (int k = 0; k < n_ent; ++k) sQ[off + k] = ent[k];
             __syncthreads();
 
-            // Compacted: the block's entries are dealt out to the threads in order.  With the
-            // ablation flag (a.no_compact) each thread instead evaluates the entries its own window
-            // found, as an uncompacted GPU-only loop would, and warps diverge on their counts.
-            const int it_end = a.no_compact ? off + n_ent : total;
-            for (int it = a.no_compact ? off : threadIdx.x; it < it_end; it += a.no_compact ? 1 : kTileQ) {
+            // Compacted: the block's entries are dealt out to the threads in order.  The ablation
+            // instantiation (NOCOMP, fc4_set_ablation) instead has each thread evaluate the entries
+            // its own window found, as an uncompacted GPU-only loop would, so warps diverge on
+            // their counts.
+            const int it_end = NOCOMP ? off + n_ent : total;
+            for (int it = NOCOMP ? off : (int)threadIdx.x; it < it_end; it += NOCOMP ? 1 : kTileQ) {
                 ++acc_ent;
                 const unsigned long long e = sQ[it];
                 const int ixe = qb + (int)(e >> 48), j1 = (int)((e >> 40) & 0xff);
@@ -524,6 +525,10 @@ cudaError_t launch4_tile(const Tables &t, const RateArgs &a, int ch, cudaStream_
     const size_t smem = tile_smem_bytes<R, NA>(t, qpt_of<ADA>(dense), ADA);
     auto kern = dense ? rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(true), BTE>
                       : rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(false), BTE>;
+    if constexpr (sizeof(R) == 4 && !BTE)       // ablation switch: mixed precision only
+        if (a.no_compact)
+            kern = dense ? rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(true), false, true>
+                         : rates4_tile_kernel<R, NA, ADA, qpt_of<ADA>(false), false, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const size_t wsmem = sizeof(C) * ((size_t)t.nc4 * 28 + NB * NB + NB + (size_t)t.n_keys * NA * 27);

@@ -94,3 +94,18 @@ def test_mesh12_partner_chunks_match_oracle(sys0, mesh12, precision, tol, chunk)
     floor = 1e-12 if precision == 0 else 1e-6
     assert_close(out[0][:, pos], G, tol, floor_frac=floor, what=f"gamma prec {precision}")
     assert_close(out[1][:, pos], WP, tol, floor_frac=floor, what=f"wp prec {precision}")
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_ablation_without_compaction_same_results(sys0, adaptive):
+    """The uncompacted divergent loop (fc4_set_ablation) evaluates the same processes: identical
+    counts, Γ equal to FP32 rounding (each thread sums different processes)."""
+    mesh = (4, 4, 4)
+    e = make_engine(sys0, mesh, precision=1)
+    sigma = 1.0 if adaptive else 0.1
+    a = [x.cpu().numpy() for x in e.rates(300.0, sigma, 31, q_subset=[3, 40], adaptive=adaptive)]
+    e.set_ablation(True)
+    b = [x.cpu().numpy() for x in e.rates(300.0, sigma, 31, q_subset=[3, 40], adaptive=adaptive)]
+    e.set_ablation(False)
+    assert np.array_equal(a[2], b[2])
+    assert_close(b[0], a[0], 1e-5, floor_frac=1e-6, what="gamma")

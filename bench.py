@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--irreducible", action="store_true",
                    help="irreducible q-points against the full mesh (see run_irreducible)")
     p.add_argument("--symmetric", action="store_true", help="--irreducible on the unperturbed crystal")
+    p.add_argument("--fp64-full", action="store_true",
+                   help="mixed and FP64 over the whole sample of the workload (one call each), one JSON line")
     p.add_argument("--ablation", action="store_true",
                    help="modes per chunk (all-modes .. mode-by-mode) and compaction ablations, one JSON line")
     p.add_argument("--cpu-sample", action="store_true",
@@ -756,6 +758,39 @@ def run_ablation(args):
     print(json.dumps(out))
 
 
+def run_fp64_full(args):
+    """Mixed and FP64 GPU paths over the whole sample of the workload (all 145 q of the precision
+    workload in one fc4_rates call each): device times, the speedup, and Γ's relative error of the
+    mixed path against FP64 per channel (R21's bar).  One JSON line."""
+    import torch
+    from paper_2510_00518_gb300 import Engine, FP64, MIXED
+    torch.cuda.set_device(0)
+    w = args.w
+    sysm, mesh = system_of(w)
+    qs = q_sample(w)
+    res, gam = {}, {}
+    for name, prec in (("mixed", MIXED), ("fp64", FP64)):
+        e = Engine(*sysm, mesh, precision=prec, timing=True)
+        e.rates(w["T"], w["sigma"], 31, q_subset=qs[:1], adaptive=w["adaptive"])        # warm
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        g = e.rates(w["T"], w["sigma"], 31, q_subset=qs, adaptive=w["adaptive"])[0]
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        kept = int(e.stats()["kept"][2:].sum())
+        res[name] = {"ms": ms, "value": kept / (ms * 1e-3), "kept_4ph": kept,
+                     "kernel_ms": {k: v for k, v in e.timings().items() if k[0] in "34"}}
+        gam[name] = g.clone()
+        e.close()
+    err = rel_err_per_channel(gam["mixed"], gam["fp64"])
+    print(json.dumps({"mode": "mixed vs FP64 over the whole sample", "workload": w["name"],
+                      "n_q": int(qs.size), "arms": res, "speedup_mixed_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"],
+                      "gamma_rel_err_mixed_vs_fp64": err, "gamma_rel_err_max": max(err),
+                      "timing": "CUDA events around one fc4_rates call per precision after a 1-q warm-up call"}))
+
+
 def run_once(args):
     """A single rates call on the first batch of the workload (profiling helper, no timing)."""
     import torch
@@ -779,6 +814,8 @@ if __name__ == "__main__":
         run_irreducible(a)
     elif a.ablation:
         run_ablation(a)
+    elif a.fp64_full:
+        run_fp64_full(a)
     elif a.once:
         run_once(a)
     elif a.batch:

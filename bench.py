@@ -595,9 +595,9 @@ def run_reference(args):
 def run_batch(args):
     """24 synthetic crystals (1x1xk diamond supercells, k = 1..4: 2-8 atoms, 6-24 branches; site
     masses U(10, 120) amu; 12^3/10^3/8^3/6^3 meshes; 4 seeded q points each; seeds 0-23; mixed
-    precision; fixed σ = 0.1 THz; T = 300 K) as one CUDA graph.  The headline runs the batch as one
-    persistent launch per cell size over a shared work list (fc4_batch_rates); the per-crystal graph
-    (each context's fc4_rates in turn) is timed beside it.  Metric: kept 4ph processes/s."""
+    precision; fixed σ = 0.1 THz; T = 300 K) as one CUDA graph, in two forms timed in turn: one
+    persistent launch per cell size over a shared work list (fc4_batch_rates), and each crystal's
+    fc4_rates in turn.  The faster form is the headline.  Metric: kept 4ph processes/s."""
     import torch
     from paper_2510_00518_gb300 import Engine, MIXED
     from paper_2510_00518_gb300.batch import BatchRunner
@@ -629,14 +629,16 @@ def run_batch(args):
         ms = timed(runner)
         kept = sum(int(e.stats()["kept"][2:].sum()) for e, _ in jobs)
         res[name] = {"ms_per_step": ms, "value": kept / (ms * 1e-3), "kept_4ph": kept}
-    head = res["persistent"]
+    best = min(res, key=lambda k: res[k]["ms_per_step"])
+    head = res[best]
     print(json.dumps({"metric": METRIC + " (batch of 24 crystals, one CUDA graph)", "value": head["value"],
                       "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": head["ms_per_step"], "higher_is_better": True, "dtype": "f32",
                       "data": "synthetic", "arms": res,
                       "config": {"workload": "batch-24-morse-supercells-6to24-branches", "q_per_crystal": args.batch_q,
                                  "meshes": "12^3/10^3/8^3/6^3 for 2/4/6/8 atoms", "graph": "one CUDA graph launch",
-                                 "four_phonon": "one persistent launch per cell size (fc4_batch_rates)",
+                                 "four_phonon": {"persistent": "one persistent launch per cell size of more than two atoms (fc4_batch_rates)",
+                                                 "per_crystal": "each crystal's fc4_rates in turn"}, "headline_arm": best,
                                  "l2": "not flushed (graph replays back to back)"}}))
 
 

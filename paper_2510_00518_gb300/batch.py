@@ -2,11 +2,12 @@
 
 Each crystal is its own fc4 context (its own cell size, mesh and clusters).  ``BatchRunner``
 runs the batch once eagerly (which sizes every buffer), then captures it on one stream into one
-CUDA graph; ``run()`` replays it with a single launch.  ``persistent=True`` (the default) captures
-one ``fc4_batch_rates`` call: the four-phonon units of all crystals of the same cell size run as one
-persistent launch over a shared work list (largest meshes first), so uneven per-crystal work
-balances over the whole GPU.  ``persistent=False`` captures every context's ``fc4_rates`` in turn
-(the tiled kernels for cells of up to two atoms).  ``autotune`` picks the general four-phonon kernel's block size per context by timing
+CUDA graph; ``run()`` replays it with a single launch.  ``persistent=False`` (the default) captures
+every context's ``fc4_rates`` in turn (the tiled kernels for cells of up to two atoms).
+``persistent=True`` captures one ``fc4_batch_rates`` call: the four-phonon units of all crystals of
+the same cell size (more than two atoms) run as one persistent launch over a shared work list
+(largest meshes first); it pays off for many small crystals, whose own launches leave the GPU
+partly idle.  ``autotune`` picks the general four-phonon kernel's block size per context by timing
 the candidates with CUDA events, and caches the choice in a JSON file keyed by the context's
 shape (atoms, mesh, precision, subset size)."""
 from __future__ import annotations
@@ -59,7 +60,7 @@ def autotune(engine, T: float, sigma_thz: float, channel_mask: int, q_subset, ca
 class BatchRunner:
     """Rates of many contexts as one CUDA graph (one launch per ``run``)."""
 
-    def __init__(self, jobs, T: float, sigma_thz: float, channel_mask: int = 31, persistent: bool = True):
+    def __init__(self, jobs, T: float, sigma_thz: float, channel_mask: int = 31, persistent: bool = False):
         """jobs: list of (engine, q_subset or None)."""
         import torch
         from . import Batch

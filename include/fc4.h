@@ -321,11 +321,11 @@ fc4_status fc4_set_ablation(fc4_ctx *ctx, int flags);
  * tables of every mode are built at fc4_init).  Kept sets do not depend on it. */
 fc4_status fc4_set_precision(fc4_ctx *ctx, int precision);
 
-/* fc4_set_tensor_cores - on = 1: in mixed precision (FC4_MIXED), two-atom cells, the
- * cluster contraction X = Σ_r P_r W_r of the 4ph +- channel runs on the tensor cores (tcgen05,
- * FP16 hi/lo operands, three products, FP32 accumulation: FP32-level accuracy).  on = 0 (the
- * default, faster on this workload): CUDA cores only.  Kept sets are identical either way; Γ agrees to rounding.  Other channels, the FP64
- * path and other cells always use the CUDA cores.  Returns FC4_ERR_INVALID for other values. */
+/* fc4_set_tensor_cores - shorthand for the FP16 x3 tensor-core format in an FC4_MIXED context:
+ * on = 1 runs the 4ph +- cluster contraction X = Σ_r P_r W_r on the tensor cores (tcgen05, FP16
+ * hi/lo operands, three products, FP32 accumulation) for two-atom cells; on = 0 (the default,
+ * faster on the measured workloads) keeps the CUDA cores.  Kept sets are identical either way; Γ
+ * agrees to rounding.  fc4_set_precision selects every format.  FC4_ERR_INVALID for other values. */
 fc4_status fc4_set_tensor_cores(fc4_ctx *ctx, int on);
 
 /* fc4_check_device - FC4_ERR_TIMEOUT if a kernel of this context gave up a bounded device-side

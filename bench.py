@@ -762,34 +762,51 @@ def run_ablation(args):
 
 def run_fp64_full(args):
     """Mixed and FP64 GPU paths over the whole sample of the workload (all 145 q of the precision
-    workload in one fc4_rates call each): device times, the speedup, and Γ's relative error of the
-    mixed path against FP64 per channel (R21's bar).  One JSON line."""
+    workload in one fc4_rates call each, channels --mask): device times, the speedup, Γ's relative
+    error of the mixed path against FP64 per channel (R21's bar), how many modes exceed 1e-4, and
+    each channel's absolute error relative to the mode's total Γ over all five channels (the
+    quantity κ sees).  One JSON line."""
     import torch
     from paper_2510_00518_gb300 import Engine, FP64, MIXED
     torch.cuda.set_device(0)
     w = args.w
     sysm, mesh = system_of(w)
     qs = q_sample(w)
+    mask = args.mask
     res, gam = {}, {}
     for name, prec in (("mixed", MIXED), ("fp64", FP64)):
         e = Engine(*sysm, mesh, precision=prec, timing=True)
-        e.rates(w["T"], w["sigma"], 31, q_subset=qs[:1], adaptive=w["adaptive"])        # warm
+        e.rates(w["T"], w["sigma"], mask, q_subset=qs[:1], adaptive=w["adaptive"])        # warm
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        g = e.rates(w["T"], w["sigma"], 31, q_subset=qs, adaptive=w["adaptive"])[0]
+        g = e.rates(w["T"], w["sigma"], mask, q_subset=qs, adaptive=w["adaptive"])[0]
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
         kept = int(e.stats()["kept"][2:].sum())
         res[name] = {"ms": ms, "value": kept / (ms * 1e-3), "kept_4ph": kept,
                      "kernel_ms": {k: v for k, v in e.timings().items() if k[0] in "34"}}
+        if name == "mixed" and mask != 31:
+            gtot = e.rates(w["T"], w["sigma"], 31, q_subset=qs, adaptive=w["adaptive"])[0].sum(0)
+        elif name == "mixed":
+            gtot = g.sum(0)
         gam[name] = g.clone()
         e.close()
     err = rel_err_per_channel(gam["mixed"], gam["fp64"])
-    print(json.dumps({"mode": "mixed vs FP64 over the whole sample", "workload": w["name"],
+    d = (gam["mixed"] - gam["fp64"]).abs()
+    floor = 1e-6 * gam["fp64"].abs().amax(dim=1, keepdim=True)
+    rel = d / torch.maximum(gam["fp64"].abs(), floor.clamp_min(1e-300))
+    n_over = (rel > 1e-4).sum(dim=1).tolist()
+    of_total = (d / gtot.abs().clamp_min(1e-300)).amax(dim=1).tolist()
+    worst = int(rel[4].argmax()) if mask & 16 else 0
+    print(json.dumps({"mode": "mixed vs FP64 over the whole sample", "workload": w["name"], "channel_mask": mask,
                       "n_q": int(qs.size), "arms": res, "speedup_mixed_vs_fp64": res["fp64"]["ms"] / res["mixed"]["ms"],
                       "gamma_rel_err_mixed_vs_fp64": err, "gamma_rel_err_max": max(err),
+                      "modes_over_1e-4": n_over, "abs_err_over_total_gamma_max": of_total,
+                      "worst_4ph--_mode": {"index": worst, "gamma_fp64": float(gam["fp64"][4, worst]),
+                                           "channel_max": float(gam["fp64"][4].abs().max()),
+                                           "total_gamma": float(gtot[worst])},
                       "timing": "CUDA events around one fc4_rates call per precision after a 1-q warm-up call"}))
 
 

@@ -240,9 +240,36 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                                 a.ad_c32 * vel_diff_norm32(t.vpT32[j2 * N + q2], t.vpTlo[j2 * N + q2], h3, l3);
                     }
                 }
+                // Adaptive ++, --: most (q'', j') have no pair near its window at all.  The necessary
+                // condition min over (j'', j''') of |Δ32| - (r_hi 2σ32 + e0) <= 0 is evaluated for all
+                // j' at once, so each width is read and scaled once per q'' instead of once per j'.
+                unsigned j1_near = vm1;
+                if constexpr (ADA) {
+                    if (ch != 3) {
+                        float mn[NB];
+#pragma unroll
+                        for (int j1 = 0; j1 < NB; ++j1) mn[j1] = 1.0f;
+#pragma unroll
+                        for (int j2 = 0; j2 < NB; ++j2) {
+                            float th[NB];
+#pragma unroll
+                            for (int j3 = 0; j3 < NB; ++j3)
+                                th[j3] = fmaf(a.ad_rhi, s_g[(j3 * NB + j2) * kTileQ + threadIdx.x], a.ad_e0);
+#pragma unroll
+                            for (int j1 = 0; j1 < NB; ++j1) {
+                                const float t2 = base32[j1] + w2f[j2];
+#pragma unroll
+                                for (int j3 = 0; j3 < NB; ++j3) mn[j1] = fminf(mn[j1], fabsf(t2 - w3f[j3]) - th[j3]);
+                            }
+                        }
+#pragma unroll
+                        for (int j1 = 0; j1 < NB; ++j1)
+                            if (!(mn[j1] <= 0.0f)) j1_near &= ~(1u << j1);
+                    }
+                }
 #pragma unroll 1
                 for (int j1 = 0; j1 < NB; ++j1) {
-                    if (!((vm1 >> j1) & 1u)) continue;
+                    if (!((j1_near >> j1) & 1u)) continue;
                     const float b = base32[j1];
                     unsigned long long okj = okm;                // tri 3: j'' >= j'
                     if (tri == 3) {
@@ -254,17 +281,6 @@ rates4_tile_kernel(const __grid_constant__ Tables t, const __grid_constant__ Rat
                     }
                     const unsigned long long tri_bits = (unsigned long long)tri << 36;
                     if constexpr (ADA) {
-                        if (ch != 3) {   // ++, --: most (q'', j') have no pair near its window at all
-                            float mn = 1.0f;
-#pragma unroll
-                            for (int j3 = 0; j3 < NB; ++j3)
-#pragma unroll
-                                for (int j2 = 0; j2 < NB; ++j2) {
-                                    const float g = s_g[(j3 * NB + j2) * kTileQ + threadIdx.x];
-                                    mn = fminf(mn, fabsf((b + w2f[j2]) - w3f[j3]) - fmaf(a.ad_rhi, g, a.ad_e0));
-                                }
-                            if (!(mn <= 0.0f)) continue;         // nothing kept, nothing ambiguous
-                        }
                         unsigned long long sure = 0, amb = 0;
 #pragma unroll
                         for (int j3 = 0; j3 < NB; ++j3)

@@ -7,7 +7,8 @@ fc4_set_modes, so both sides see the same ω bits and eigenvector gauge.
                        700 K; the GPU computes every mode of the mesh in one call (the bench's
                        launch configuration) and the sampled modes are compared
   config3_16cubed.npz  16x16x16 mesh, seed 1, adaptive σ (scale 1), 300 K, the first of the 145
-                       sampled q x 6 branches
+                       sampled q x 6 branches; computed alone and inside the first 29 of the 145 q
+                       (one step of bench.py)
 Counts must match bit for bit; Γ and WP within 1e-10 (FP64), within 1e-4 (mixed, FP32 CUDA
 cores; TF32 x3 tensor cores) of max(|ref|, 1e-6 x the channel's largest value)."""
 import os
@@ -77,3 +78,23 @@ def test_config3_sampled_q_against_oracle(precision, tol):
     out = [x.cpu().numpy() for x in e.rates(float(g["T"][0]), float(g["sigma"]), 31, q_subset=qs, adaptive=True)]
     e.check_device()
     compare(out, g, 0, tol)
+
+
+def test_config3_bench_step_against_oracle():
+    """The stored q inside the bench's own launch: one mixed call on the first 29 of the 145 sampled
+    q (default_rng(1).choice(4096, 145), sorted; the stored q is the first).  Its columns must match
+    the oracle's values, and equal bit for bit the same q computed alone: every block owns one
+    (λ, q') unit and each mode's partials are summed in a fixed order, so the other modes of a call
+    do not change a mode's result."""
+    from synth.sampling import sample_q
+    g = load("config3_16cubed.npz")
+    step = sample_q(4096, 145, 1)[:29]
+    assert int(step[0]) == int(g["q"][0])
+    e = engine(g, 1)
+    args = (float(g["T"][0]), float(g["sigma"]), 31)
+    full = [x.cpu().numpy()[:, :6] for x in e.rates(*args, q_subset=step, adaptive=True)]
+    alone = [x.cpu().numpy() for x in e.rates(*args, q_subset=step[:1], adaptive=True)]
+    e.check_device()
+    for a, b in zip(full, alone):
+        assert np.array_equal(a, b)
+    compare(full, g, 0, 1e-4)

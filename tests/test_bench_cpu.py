@@ -41,3 +41,24 @@ def test_one_core_oracle_sample_and_host_info():
     assert d is not None and d["cores"] == 1 and d["value"] > 0 and "q' < 2" in d["sample"]
     model, n = bench.cpu_host_info()
     assert model and n >= 1
+
+
+def test_default_steps_cover_the_sample_evenly():
+    """The default step of the precision workload takes 29 of the 145 sampled q: the 5 batches
+    partition the sample, so any multiple of 5 timed steps weights every q equally; the arms use
+    its first 5 q."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sys_argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+    finally:
+        sys.argv = sys_argv
+    assert a.q_per_step == 29 and a.w["n_sample"] == 145
+    bl = bench.batches(a.w, a.q_per_step)
+    assert len(bl) == 5 and all(len(b) == 29 for b in bl)
+    allq = sorted(int(q) for b in bl for q in b)
+    assert allq == sorted(int(q) for q in bench.q_sample(a.w)) and len(set(allq)) == 145
+    assert bench.ARM_Q == 5
+    assert a.w["name"] == "morse-diamond-2atom-16x16x16-145q-adaptive-sigma"
